@@ -1,0 +1,88 @@
+/*
+ * mc_oracle.h -- declarations of the CPU oracle (test infrastructure only;
+ * see mc_oracle.c).  Nothing in the CUDA library includes this header.
+ */
+#ifndef MC_ORACLE_H
+#define MC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* LCG parameters of Eq. (1): X_{n+1} = (g X_n + c) mod 2^m. */
+typedef struct {
+    uint32_t m;
+    uint32_t pad;
+    uint64_t g;
+    uint64_t c;
+} or_lcg;
+
+enum { OR_SEED_HASH = 0, OR_SEED_STRIDE = 1, OR_SEED_HASH_HIER = 2 };
+enum { OR_SRC_ISOTROPIC = 0, OR_SRC_BEAM = 1 };
+
+/* One slab problem.  seed: hash mode = global seed s; stride mode = X_0. */
+typedef struct {
+    double L, sigma_t, c;
+    uint64_t n_histories;
+    uint64_t seed;
+    uint64_t stride_q;     /* stride Q; also the nominal stride for exceedance counts */
+    uint64_t id_offset;    /* stride mode: unit index of local history 0 */
+    uint64_t key;          /* hierarchical hash: key i of hash(j, hash(i, s)) */
+    uint64_t tally_offset; /* first int64 slot of this problem's [batch][bin] tally */
+    uint32_t n_bins, n_batches;
+    uint32_t source, seeding;
+} or_slab_problem;
+
+/* Indices into a per-problem uint64 counter block of OR_NCOUNT entries. */
+enum {
+    OR_C_SOURCE = 0,
+    OR_C_FLIGHTS,
+    OR_C_COLLISIONS,
+    OR_C_ABSORPTIONS,
+    OR_C_SCATTERS,
+    OR_C_LEAK_LO,
+    OR_C_LEAK_HI,
+    OR_C_DRAWS,
+    OR_C_EXCEED_HIST,
+    OR_C_EXCEED_DRAWS,
+    OR_C_SPLITS,
+    OR_C_ROULETTE_KILLS,
+    OR_C_CAPPED,
+    OR_C_MAX_DRAWS,
+    OR_C_CHILDREN,
+    OR_C_RESERVED,
+    OR_NCOUNT
+};
+
+uint64_t or_mask(uint32_t m);
+uint64_t or_lcg_next(uint64_t x, uint32_t m, uint64_t g, uint64_t c);
+double or_u01(uint64_t x, uint32_t m);
+uint64_t or_lcg_skip(uint64_t x0, uint64_t k, uint32_t m, uint64_t g, uint64_t c);
+uint64_t or_stride_seed(uint64_t x0, uint64_t q, uint64_t k, uint32_t m, uint64_t g, uint64_t c);
+uint64_t or_subhash(uint64_t x);
+uint64_t or_hash(uint64_t k, uint64_t s);
+uint64_t or_hash_seed(uint64_t k, uint64_t s, uint32_t m);
+void or_seed_hash(uint32_t m, uint64_t parent, uint64_t key_begin, uint64_t count, uint64_t* out);
+void or_seed_stride(uint32_t m, uint64_t g, uint64_t c, uint64_t x0, uint64_t q, uint64_t id_begin,
+                    uint64_t count, uint64_t* out);
+void or_lcg_draw(uint32_t m, uint64_t g, uint64_t c, uint64_t* states, uint64_t n, uint32_t draws,
+                 double* u, uint64_t* digest);
+
+uint64_t or_slab_seed(const or_lcg* l, const or_slab_problem* p, uint64_t id);
+uint64_t or_batch_of(uint64_t id, uint64_t n_histories, uint32_t n_batches);
+int or_slab_run(const or_lcg* l, const or_slab_problem* p, uint64_t id_begin, uint64_t id_end,
+                uint64_t event_cap, int64_t* tally, double* tally_fp, uint64_t* counts,
+                uint64_t* hist_state, uint64_t* hist_draws);
+
+double or_norm_cdf(double z);
+double or_norm_ppf(double p);
+int or_shapiro_wilk(const double* x, int n, double* w, double* p);
+int or_batch_stats(const double* x, uint32_t n_batches, uint32_t n_points, double* z, double* w,
+                   double* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
