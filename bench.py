@@ -1,0 +1,437 @@
+#!/usr/bin/env python3
+"""Benchmark of the hash- vs stride-seeded LCG path on GB300.
+
+One step = the whole RNG microbenchmark workload on each GPU: 2^26 streams
+(history ids rank*2^26 .. (rank+1)*2^26-1), each seeded by hash (s = 42) and,
+separately, by stride (X0 = 1, Q = 152917), each drawing 64 uniforms through
+libmc's fused seed+draw kernel, which writes every stream's final state and
+the digest of its draws.  value = draws per second over all ranks.
+
+Also reported: the dominant kernel's roofline (integer-issue bound), the
+oracle on the host cores (cpu_baseline), an end-to-end number through the
+public API including the device-to-host copy of every result, SM clocks
+sampled during the timed region, and a `detail` object with seeding-only
+rates and slab-transport histories/s (fp64 and fp32-guarded, single and
+batched problems).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("particle histories/sec and RNG draws/sec on 1 GB300 "
+          "(hash vs stride, % int-pipe roofline)")
+N_STREAMS = 2**26
+DRAWS = 64
+# Integer instructions per draw of the formulation in csrc/mc_device.cuh:
+# 64-bit multiply-add as IMAD.WIDE + 2 IMAD (3); extraction of the top 53 of
+# 63 state bits (2); exact integer-to-fp64 assembly: nonzero test, clz,
+# shift amount, funnel shift, shift, exponent, add (7); 64-bit digest add (2).
+OPS_PER_DRAW = 14
+RECIPE_SM_MAX_MHZ = 2070.0
+LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def int_issue_peak(num_sms):
+    """Integer-issue roofline: every SM issues one warp instruction per clock
+    on each of its 4 sub-partitions (128 lane-ops), at the recipe's maximum
+    SM clock.  Returns lane-ops per second."""
+    return num_sms * LANES_PER_SM_PER_CLK * RECIPE_SM_MAX_MHZ * 1e6
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# --------------------------------------------------------------------------- CPU
+
+def oracle_draw_rate(target_cpu_s=12.0, threads=None):
+    """The oracle (as it stands) on the host cores: hash- and stride-seeded
+    streams, 64 draws each, on a bounded sample of the microbenchmark's ids.
+    Returns (draws/s, threads, sample description)."""
+    import oracle as O
+    from paper_2403_06362_gb300 import workloads as W
+    O.build()
+    threads = threads or os.cpu_count() or 1
+
+    def work(n, id0, out):
+        a = O.seed_hash(W.LCG_M, W.HASH_SEED, id0, n)
+        O.lcg_draw(W.LCG_M, W.LCG_G, W.LCG_C, a, DRAWS, want_u=False)
+        b = O.seed_stride(W.LCG_M, W.LCG_G, W.LCG_C, W.STRIDE_X0, W.STRIDE_Q, id0, n)
+        O.lcg_draw(W.LCG_M, W.LCG_G, W.LCG_C, b, DRAWS, want_u=False)
+        out.append(n)
+
+    t = time.perf_counter()
+    work(4096, 0, [])
+    per_stream = (time.perf_counter() - t) / 4096
+    n_total = int(max(threads * 4096, min(N_STREAMS, target_cpu_s / per_stream)))
+    per = n_total // threads
+    ths, outs = [], []
+    t = time.perf_counter()
+    for i in range(threads):
+        th = threading.Thread(target=work, args=(per, i * per, outs))
+        th.start()
+        ths.append(th)
+    for th in ths:
+        th.join()
+    dt = time.perf_counter() - t
+    draws = 2 * per * threads * DRAWS
+    return draws / dt, threads, f"{per * threads} of the 2^26 ids (hash and stride), 64 draws each, {dt:.1f} s"
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2403_06362_gb300 import workloads as W
+    O.build()
+    threads = os.cpu_count() or 1
+    per = 2**15  # streams per thread per step and mode
+    times = []
+
+    def work(id0, n):
+        a = O.seed_hash(W.LCG_M, W.HASH_SEED, id0, n)
+        O.lcg_draw(W.LCG_M, W.LCG_G, W.LCG_C, a, DRAWS, want_u=False)
+        b = O.seed_stride(W.LCG_M, W.LCG_G, W.LCG_C, W.STRIDE_X0, W.STRIDE_Q, id0, n)
+        O.lcg_draw(W.LCG_M, W.LCG_G, W.LCG_C, b, DRAWS, want_u=False)
+
+    def step(k):
+        ths = [threading.Thread(target=work, args=(((k * threads + i) * per) % N_STREAMS, per))
+               for i in range(threads)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+
+    for k in range(args.warmup):
+        step(k)
+    for k in range(args.steps):
+        t = time.perf_counter()
+        step(args.warmup + k)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    draws = 2 * per * threads * DRAWS
+    value = draws / (ms / 1e3)
+    sample = f"{per * threads} streams per mode per step (of 2^26), 64 draws each"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_block(),
+        "cpu_baseline": {"value": value, "unit": "draws/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "draws/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def config_block():
+    return {"workload": "rng microbenchmark: 2^26 streams per GPU (history ids), 64 uniforms each, "
+                        "hash seeds (s=42) and stride seeds (X0=1, Q=152917), m=63 LCG "
+                        "g=2806196910506780709 c=1; fused seed+draw, final state + digest per stream",
+            "streams_per_gpu": N_STREAMS, "draws_per_stream": DRAWS, "modes": ["hash", "stride"],
+            "l2": "L2 flushed before every step (256 MiB write); the step writes 1 GiB per mode"}
+
+
+# --------------------------------------------------------------------------- GPU
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-detail", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2403_06362_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import workloads as W
+
+    ctx = mc.Context(local)
+    lcg = mc.make_lcg()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = N_STREAMS
+    id0 = rank * n
+    specs = [mc.mc_seed_spec(mode=mc.MC_SEED_HASH, seed=W.HASH_SEED),
+             mc.mc_seed_spec(mode=mc.MC_SEED_STRIDE, seed=W.STRIDE_X0, stride_q=W.STRIDE_Q)]
+    st = [torch.empty(n, dtype=torch.int64, device=dev) for _ in specs]
+    dg = [torch.empty(n, dtype=torch.int64, device=dev) for _ in specs]
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.int32, device=dev)
+
+    def launch(i):
+        mc.mc_lcg_draw(ctx, lcg, specs[i], id0, st[i], n, DRAWS, None, dg[i], stream)
+
+    for _ in range(args.warmup):
+        launch(0)
+        launch(1)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.25)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        launch(0)
+        ev[k][1].record(stream)
+        launch(1)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_hash = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_str = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    ms_step = (sum(t_hash) + sum(t_str)) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    draws_per_step = 2 * n * DRAWS * world
+    value = draws_per_step / (ms_step / 1e3)
+
+    # Roofline of the dominant kernel (the fused seed+draw kernel): integer
+    # issue.  achieved = hand-counted ops per draw x draws per launch / mean
+    # launch time.
+    props = torch.cuda.get_device_properties(dev)
+    launch_ms = statistics.mean(t_hash + t_str)
+    achieved = OPS_PER_DRAW * n * DRAWS / (launch_ms / 1e3)
+    peak = int_issue_peak(props.multi_processor_count)
+    roofline = {"bound": "alu", "kernel": "draw_kernel (fused seed + 64 draws)",
+                "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {RECIPE_SM_MAX_MHZ:.0f} MHz",
+                "ops_per_draw": OPS_PER_DRAW}
+
+    # End to end through the public call: device results copied to pinned
+    # host memory inside the timed region, every step.
+    h_st = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
+    h_dg = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
+    e2e_steps = max(3, min(20, args.steps))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(e2e_steps):
+        for i in range(2):
+            launch(i)
+            h_st[i].copy_(st[i], non_blocking=True)
+            h_dg[i].copy_(dg[i], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": draws_per_step / (e2e_ms / 1e3), "unit": "draws/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": 2 * 2 * n * 8,
+           "note": "inputs are scalars (seed, id range); every final state and digest is copied to host"}
+
+    detail = {"draws_per_s_hash": n * DRAWS * world / (statistics.mean(t_hash) / 1e3),
+              "draws_per_s_stride": n * DRAWS * world / (statistics.mean(t_str) / 1e3),
+              "ms_hash": statistics.mean(t_hash), "ms_stride": statistics.mean(t_str)}
+    if not args.no_detail and rank == 0:
+        detail.update(seeding_detail(mc, ctx, lcg, torch, dev, stream))
+        detail.update(transport_detail(mc, ctx, lcg, torch, dev, stream, W))
+
+    del st, dg, flush
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = oracle_draw_rate()
+        cpu = {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "draws/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": config_block(),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 2 * args.steps, "detail": detail,
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def seeding_detail(mc, ctx, lcg, torch, dev, stream):
+    """Seeding only (mc_seed_hash / mc_seed_stride), HBM-store bound:
+    8 bytes written per stream."""
+    peaks, src = measured_peaks()
+    n = N_STREAMS
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    res = {}
+    for name, fn in (("hash", lambda: mc.mc_seed_hash(ctx, lcg, 42, 0, n, out, stream)),
+                     ("stride", lambda: mc.mc_seed_stride(ctx, lcg, 1, 152917, 0, n, out, stream))):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
+        gbs = n * 8 / (ms / 1e3) / 1e9
+        res[f"seeds_per_s_{name}"] = n / (ms / 1e3)
+        res[f"seed_{name}_hbm"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                   "frac": gbs / peaks["hbm_gbs"], "peak_source": src}
+    return res
+
+
+def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
+    """Slab transport histories/s: the 10^4-history slab, the 10^6-history
+    long-chain slab (fp64 and fp32-guarded, hash and stride), and the 256
+    batched problems (one fp32 launch vs one fp64 launch per problem)."""
+    res = {}
+
+    def timed(probs, reps=2, **cfgkw):
+        tally = mc.Tally(W.tally_slots(probs), len(probs))
+        cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+        cfg = mc.mc_run_config(**cfgkw)
+        mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        return best, tally, cp
+
+    for name, probs in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
+        for sname, s in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
+            for prec in (0, 1):
+                p = probs(s)
+                ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, precision=prec)
+                key = f"{name}_{sname}_{'fp32' if prec else 'fp64'}"
+                r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
+                res[key] = {"ms": ms, "histories_per_s": p[0]["n_histories"] / (ms / 1e3),
+                            "flights_per_s": r.counts["flights"] / (ms / 1e3),
+                            "exceed_hist": r.counts["exceed_hist"], "max_draws": r.counts["max_draws"]}
+    probs = W.slab_batched(W.SEED_HASH_HIER)
+    nh = sum(p["n_histories"] for p in probs)
+    ms32, _, _ = timed(probs, reps=2, precision=1)
+    ms64, _, _ = timed(probs, reps=1, precision=0)
+    # the plain fp64 single-problem path: one launch per problem
+    t0 = time.perf_counter()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tallies = []
+    for p in probs:
+        q = dict(p)
+        q["tally_offset"] = 0
+        tallies.append((mc.Tally(W.tally_slots([q]), 1), mc.problem_array([W.to_mc_problem(q, mc)])))
+    a.record(stream)
+    for tl, cp in tallies:
+        mc.mc_transport_run(ctx, lcg, cp, mc.mc_run_config(), tl.c, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_single = a.elapsed_time(b)
+    _ = t0
+    res["slab_batched"] = {"histories": nh, "ms_batched_fp32": ms32, "ms_batched_fp64": ms64,
+                           "ms_single_fp64_loop": ms_single,
+                           "histories_per_s_batched_fp32": nh / (ms32 / 1e3),
+                           "speedup_batched_fp32_over_single_fp64": ms_single / ms32}
+    return res
+
+
+if __name__ == "__main__":
+    main()

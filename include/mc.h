@@ -1,0 +1,253 @@
+/*
+ * mc.h -- C ABI of libmc, a GB300 (sm_103a) library for history-based Monte
+ * Carlo particle transport in which every particle history owns one LCG
+ * stream, seeded either by hashing (the method of Cuneo & Variansyah, "An
+ * Alternative to Stride-Based RNG for Monte Carlo Transport", arXiv
+ * 2403.06362) or by striding with Brown's skip-ahead (the baseline the
+ * paper compares against).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are
+ *     host pointers owned by the caller.  The library never frees caller
+ *     memory and never keeps a caller pointer after a call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it and the call returns without
+ *     waiting, except where a call says it synchronises.
+ *   - Every call returns an int status: MC_OK (0) or a negative MC_ERR_*.
+ *     mc_last_error() gives a message for the calling thread's last error.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *   - LCG states are m-bit integers stored in uint64_t (high bits zero).
+ *   - A "uniform" is u = floor(X / 2^(m-53)) * 2^-53 in [0,1) as an IEEE
+ *     double (for m < 53: X * 2^-m), taken from the state AFTER each step:
+ *     the seed itself is never an output (Section 2, Eq. 1: the next state
+ *     "also serves as the output").
+ *   - Every call is bit-reproducible: results depend on the inputs only,
+ *     never on launch shape, schedule or timing.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MC_API __attribute__((visibility("default")))
+#else
+#define MC_API
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+    MC_OK = 0,
+    MC_ERR_ARG = -1,       /* invalid argument (checked on the host)          */
+    MC_ERR_CUDA = -2,      /* a CUDA runtime call failed                      */
+    MC_ERR_OVERFLOW = -3,  /* a tally bin left the int64 headroom (2^62)      */
+    MC_ERR_EVENT_CAP = -4, /* some history hit the per-history event cap      */
+    MC_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                   */
+    MC_ERR_CAPACITY = -6,  /* a bounded device buffer (secondary bank) filled */
+    MC_ERR_STATE = -7      /* call out of order (e.g. no context)             */
+};
+
+/* Thread-local message describing the last failing call of this thread. */
+MC_API const char* mc_last_error(void);
+
+/* ------------------------------------------------------------- LCG (Eq. 1)
+ * X_{n+1} = (g X_n + c) mod 2^m, 1 <= m <= 64.  g must be odd (an even g
+ * has no skip-ahead inverse and no full period).  The workload parameters
+ * are m = 63, g = 2806196910506780709, c = 1 (MCNP5's 63-bit generator,
+ * full period since c is odd and g = 1 mod 4). */
+typedef struct {
+    uint32_t m;
+    uint32_t reserved; /* must be 0 */
+    uint64_t g;
+    uint64_t c;
+} mc_lcg;
+
+/* --------------------------------------------------------------- context
+ * A context owns the library's scratch memory on one device: work-queue
+ * tickets, the status word, the device copy of the problem list and the
+ * particle banks of the event-based schedule.  Create it once, outside any
+ * timed or captured region; it allocates device memory.  A context may be
+ * used from one host thread at a time. */
+typedef struct mc_ctx mc_ctx;
+
+/* Creates a context on `device` (the device is made current).  *out is set
+ * on success.  Errors: MC_ERR_ARG (out NULL), MC_ERR_CUDA. */
+MC_API int mc_ctx_create(mc_ctx** out, int device);
+/* Frees the context and its device memory (synchronises the device). */
+MC_API void mc_ctx_destroy(mc_ctx* ctx);
+
+/* ---------------------------------------------------------- hash seeding
+ * Section 4, Listing 1 and Eq. (3): d_states[i] = hash(key_begin + i,
+ * parent_seed) mod 2^m, where hash is the modified murmur_hash64a of
+ * Listing 1 (64-bit key and seed, wrapping 64-bit products).  For the
+ * hierarchical seeds of Eq. (4) pass parent_seed = hash(i, s) (see
+ * mc_hash64).  d_states: uint64_t[count], any alignment of 8 bytes; written
+ * with coalesced 16-byte stores where aligned.  count = 0 is a no-op.
+ * Errors: MC_ERR_ARG (ctx/lcg/d_states NULL with count > 0, bad lcg). */
+MC_API int mc_seed_hash(mc_ctx* ctx, const mc_lcg* lcg, uint64_t parent_seed, uint64_t key_begin,
+                        uint64_t count, uint64_t* d_states, void* stream);
+
+/* -------------------------------------------------------- stride seeding
+ * Section 3, Eq. (2): d_states[i] = X_{Q*(id_begin+i)}, the state reached
+ * from X_0 = x0 after Q*(id_begin+i) LCG steps (unit k gets X_{Qk}; unit 0
+ * gets x0 itself).  Computed by Brown's binary skip-ahead, evaluated on the
+ * device; the step count is taken mod 2^64, which is exact because the
+ * affine map of 2^64 steps is the identity mod 2^64 for odd g.
+ * Errors: as mc_seed_hash; stride_q = 0 is allowed (all states = x0). */
+MC_API int mc_seed_stride(mc_ctx* ctx, const mc_lcg* lcg, uint64_t x0, uint64_t stride_q,
+                          uint64_t id_begin, uint64_t count, uint64_t* d_states, void* stream);
+
+/* ----------------------------------------------------------------- draws
+ * Advances n_streams streams by `draws` steps each (Eq. 1) and reports the
+ * uniforms.  Draw j of stream i is the uniform of the stream's (j+1)-th
+ * state.
+ *   seed      NULL: d_states holds the n_streams input states and is
+ *             overwritten with the final states.
+ *             non-NULL: the streams are seeded in the kernel, stream i with
+ *             the seed of unit id_begin + i (fused seeding + draws); d_states
+ *             (nullable) receives the final states.
+ *   d_u       nullable; double[draws][n_streams] (draw-major: d_u[j*n+i]).
+ *   d_digest  nullable; uint64_t[n_streams]; the wrapping 64-bit sum of the
+ *             IEEE-754 bit patterns of the stream's draws (lets a caller
+ *             consume every draw without storing it).
+ * Errors: MC_ERR_ARG (bad lcg or seed spec, d_states NULL without seed). */
+typedef struct {
+    uint32_t mode;     /* MC_SEED_HASH, MC_SEED_STRIDE or MC_SEED_HASH_HIER */
+    uint32_t reserved; /* must be 0 */
+    uint64_t seed;     /* hash: global seed s; stride: X_0 */
+    uint64_t stride_q; /* stride: Q */
+    uint64_t key;      /* hierarchical hash: key i of hash(j, hash(i, s)) */
+} mc_seed_spec;
+
+MC_API int mc_lcg_draw(mc_ctx* ctx, const mc_lcg* lcg, const mc_seed_spec* seed, uint64_t id_begin,
+                       uint64_t* d_states, uint64_t n_streams, uint32_t draws, double* d_u,
+                       uint64_t* d_digest, void* stream);
+
+/* --------------------------------------------------------------- transport
+ * History-based (or event-based) one-speed transport in a slab, or
+ * multigroup transport in a two-region box; every source history owns one
+ * LCG stream seeded by hash or stride, and secondaries created by splitting
+ * are seeded on demand by S_c = hash(k, S_p) (Section 4, Eq. 5).
+ * Flux tallies are track-length estimates accumulated as int64 fixed point
+ * (scale 2^32, one llrint per contribution), so totals are independent of
+ * scheduling and bit-identical across launch shapes and schedules. */
+enum { MC_SEED_HASH = 0, MC_SEED_STRIDE = 1, MC_SEED_HASH_HIER = 2 };
+enum { MC_SRC_ISOTROPIC = 0, MC_SRC_BEAM = 1 };
+enum { MC_GEOM_SLAB = 0, MC_GEOM_BOX = 1 };
+enum { MC_FP64 = 0, MC_FP32_GUARDED = 1 };
+enum { MC_SCHED_HISTORY = 0, MC_SCHED_EVENT = 1, MC_SCHED_AUTO = 2 };
+
+/* Box problem data (geometry MC_GEOM_BOX); host memory, read during the call. */
+#define MC_BOX_MAX_GROUPS 8
+typedef struct {
+    double side;                      /* cube [0,side]^3                           */
+    double inner_lo, inner_hi;        /* inner region [inner_lo,inner_hi]^3        */
+    double sigma_t[2];                /* per region: 0 = outer, 1 = inner          */
+    double c[2];                      /* scattering ratio per region               */
+    double ww_low[2], ww_high[2], ww_survive[2]; /* weight window per region       */
+    double scatter_cdf[2][MC_BOX_MAX_GROUPS][MC_BOX_MAX_GROUPS]; /* [r][g][g'] CDF */
+    uint32_t n_groups;
+    uint32_t mesh;                    /* mesh cells per axis (tally [mesh]^3)      */
+    uint32_t max_split;               /* cap on n of one split                     */
+    uint32_t reserved;
+} mc_box_spec;
+
+typedef struct {
+    uint32_t geometry;    /* MC_GEOM_SLAB or MC_GEOM_BOX                           */
+    uint32_t source;      /* MC_SRC_ISOTROPIC (uniform in the slab/box) or BEAM   */
+    uint32_t seeding;     /* MC_SEED_HASH, MC_SEED_STRIDE, MC_SEED_HASH_HIER       */
+    uint32_t n_bins;      /* slab: equal-width bins over [0,L]; box: mesh^3        */
+    uint32_t n_batches;   /* contiguous history-id batches (>= 1)                  */
+    uint32_t reserved;
+    double L;             /* slab thickness                                        */
+    double sigma_t;       /* slab total cross section                              */
+    double c;             /* slab scattering ratio                                 */
+    uint64_t n_histories; /* source histories, local ids 0..n-1                    */
+    uint64_t seed;        /* hash: global seed s; stride: X_0                      */
+    uint64_t stride_q;    /* stride Q (also the nominal stride for exceedance)     */
+    uint64_t id_offset;   /* stride: unit index of local history 0                 */
+    uint64_t key;         /* hierarchical hash key i                               */
+    uint64_t tally_offset;/* first int64 slot of this problem: [batch][bin]        */
+    const mc_box_spec* box; /* geometry MC_GEOM_BOX only                           */
+} mc_problem;
+
+typedef struct {
+    uint32_t schedule;      /* MC_SCHED_HISTORY, MC_SCHED_EVENT, MC_SCHED_AUTO    */
+    uint32_t precision;     /* MC_FP64 or MC_FP32_GUARDED (flight and geometry)   */
+    uint32_t block;         /* threads per block; 0 = library default             */
+    uint32_t chunk;         /* histories a warp takes per ticket grab; 0 = 128    */
+    uint32_t blocks_per_sm; /* 0 = from the occupancy calculator                  */
+    uint32_t use_graph;     /* 1 = capture the launch sequence once and replay    */
+    uint32_t accumulate;    /* 0 = zero tallies and counts first; 1 = add to them */
+    uint32_t tally_mode;    /* 0 = auto, 1 = stage all slots in shared memory,    */
+                            /* 2 = global atomics only (results are identical)    */
+    uint64_t event_cap;     /* per-history flight cap; 0 = 2^40                   */
+    uint64_t range_begin;   /* run only global histories [begin,end) of the       */
+    uint64_t range_end;     /* concatenated problems; end 0 = all                 */
+} mc_run_config;
+
+/* Counter block per problem: uint64_t[MC_NCOUNT], exact integers. */
+enum {
+    MC_C_SOURCE = 0, MC_C_FLIGHTS, MC_C_COLLISIONS, MC_C_ABSORPTIONS, MC_C_SCATTERS,
+    MC_C_LEAK_LO, MC_C_LEAK_HI, MC_C_DRAWS, MC_C_EXCEED_HIST, MC_C_EXCEED_DRAWS,
+    MC_C_SPLITS, MC_C_ROULETTE_KILLS, MC_C_CAPPED, MC_C_MAX_DRAWS, MC_C_CHILDREN,
+    MC_C_RESERVED, MC_NCOUNT
+};
+
+typedef struct {
+    int64_t* d_bins;        /* device int64[n_slots], fixed point 2^-32         */
+    uint64_t n_slots;
+    uint64_t* d_counts;     /* device uint64[n_problems][MC_NCOUNT]             */
+    uint64_t* d_hist_state; /* nullable device uint64[total histories]: final   */
+    uint64_t* d_hist_draws; /* state / draw count per source history, indexed   */
+                            /* by global history index (problem prefix + id)    */
+} mc_tally;
+
+/* Runs every history of the n_problems problems (or config->range) and
+ * accumulates track-length tallies and counters.  Problems and the box
+ * spec are host memory read during the call (copied to the context).
+ * The call enqueues work on `stream` and returns; the device status word
+ * is checked by mc_tally_read.  Errors: MC_ERR_ARG (bad problem: L, sigma_t
+ * <= 0, c outside [0,1], n_bins or n_batches 0, slots outside the tally),
+ * MC_ERR_CUDA. */
+MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
+                            uint32_t n_problems, const mc_run_config* config, const mc_tally* tally,
+                            void* stream);
+
+/* Reads problem `problem`'s tally back (synchronises `stream`).
+ *   h_flux      double[n_bins]: flux per source history and unit volume,
+ *               phi_b = sum_b * 2^-32 / (N * V_b), over all batches.
+ *   h_rel_err   nullable double[n_bins]: relative standard error of phi_b
+ *               from the batch means (0 when n_batches < 2).
+ *   h_batch     nullable double[n_batches][n_bins]: phi per batch.
+ *   h_raw       nullable int64_t[n_batches][n_bins]: raw fixed point.
+ *   h_counts    nullable uint64_t[MC_NCOUNT].
+ * Errors: MC_ERR_ARG, MC_ERR_CUDA, MC_ERR_OVERFLOW (|bin| >= 2^62),
+ * MC_ERR_EVENT_CAP (a history was capped), MC_ERR_CAPACITY. */
+MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t problem,
+                         const mc_tally* tally, double* h_flux, double* h_rel_err, double* h_batch,
+                         int64_t* h_raw, uint64_t* h_counts, void* stream);
+
+/* ---------------------------------------------------------- host helpers */
+
+/* Listing 1 on the host: hash(k, s) as a full 64-bit value (e.g. the parent
+ * seed hash(i, s) of Eq. 4). */
+MC_API uint64_t mc_hash64(uint64_t k, uint64_t s);
+
+/* Section 5 normality procedure on host data x[n_batches][n_points]: the
+ * normalised deviations z = (x - mean)/sd per point (sd with n-1) and the
+ * Shapiro-Wilk W and p-value of each point's batch values (Royston's
+ * approximation, 3 <= n_batches <= 5000).  z, w, p nullable.
+ * Errors: MC_ERR_ARG (n_batches outside [3,5000]; a point with zero spread
+ * gets W = p = NaN and the call returns MC_ERR_ARG after filling the rest). */
+MC_API int mc_normality(const double* h_x, uint32_t n_batches, uint32_t n_points, double* h_z,
+                        double* h_w, double* h_p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

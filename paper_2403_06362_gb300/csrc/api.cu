@@ -1,0 +1,319 @@
+// api.cu -- contexts, errors, the transport front end and the tally read-back
+// of libmc.  The device work lives in rng.cu and slab.cu; this file is host
+// logic only: argument checks, staging of the problem list, launch sequence
+// and conversion of int64 fixed-point tallies to flux.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "mc_device.cuh"
+#include "transport.h"
+
+namespace mci {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MC_OK;
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return MC_ERR_CUDA;
+}
+
+int check_lcg(const mc_lcg* lcg) {
+  if (!lcg) {
+    set_error("lcg is NULL");
+    return MC_ERR_ARG;
+  }
+  if (lcg->m < 1 || lcg->m > 64 || lcg->reserved != 0) {
+    set_error("lcg: m = %u outside 1..64 (or reserved != 0)", lcg->m);
+    return MC_ERR_ARG;
+  }
+  if ((lcg->g & 1ull) == 0) {
+    set_error("lcg: g must be odd");
+    return MC_ERR_ARG;
+  }
+  return MC_OK;
+}
+
+int DeviceBuf::reserve(size_t want) {
+  if (want <= bytes) return MC_OK;
+  release();
+  void* p = nullptr;
+  int st = cuda_status(cudaMalloc(&p, want), "cudaMalloc(context scratch)");
+  if (st != MC_OK) return st;
+  ptr = p;
+  bytes = want;
+  return MC_OK;
+}
+
+void DeviceBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+}  // namespace mci
+
+namespace {
+
+// Layout of the small scratch block.
+constexpr size_t kTicketOff = 0;     // unsigned long long ticket
+constexpr size_t kScratchBytes = 256;
+
+int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStream_t s) {
+  const size_t bytes = (size_t)n * mci::slab_dev_size();
+  cudaEvent_t* ev = &ctx->staged;
+  if (*ev) MC_TRY_CUDA(cudaEventSynchronize(*ev));
+  if (bytes > ctx->h_problems_bytes) {
+    if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
+    ctx->h_problems = nullptr;
+    ctx->h_problems_bytes = 0;
+    MC_TRY_CUDA(cudaMallocHost(&ctx->h_problems, bytes));
+    ctx->h_problems_bytes = bytes;
+  }
+  int st = ctx->problems.reserve(bytes);
+  if (st != MC_OK) return st;
+  mci::slab_fill_host(problems, n, ctx->h_problems);
+  MC_TRY_CUDA(cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, s));
+  if (!*ev) MC_TRY_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  MC_TRY_CUDA(cudaEventRecord(*ev, s));
+  return mci::slab_prep(ctx->problems.ptr, n, s);
+}
+
+int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t* total) {
+  uint64_t acc = 0;
+  for (uint32_t i = 0; i < n; ++i) {
+    const mc_problem& q = p[i];
+    if (q.geometry != MC_GEOM_SLAB) {
+      mci::set_error("problem %u: only slab geometry is supported by this entry point", i);
+      return MC_ERR_ARG;
+    }
+    if (!(q.L > 0.0) || !(q.sigma_t > 0.0) || !(q.c >= 0.0 && q.c <= 1.0) || !std::isfinite(q.L) ||
+        !std::isfinite(q.sigma_t)) {
+      mci::set_error("problem %u: need L > 0, sigma_t > 0, 0 <= c <= 1", i);
+      return MC_ERR_ARG;
+    }
+    if (q.n_bins == 0 || q.n_batches == 0 || q.source > MC_SRC_BEAM || q.seeding > MC_SEED_HASH_HIER ||
+        q.reserved != 0) {
+      mci::set_error("problem %u: bad n_bins/n_batches/source/seeding", i);
+      return MC_ERR_ARG;
+    }
+    const uint64_t slots = (uint64_t)q.n_bins * q.n_batches;
+    if (q.tally_offset > t->n_slots || slots > t->n_slots - q.tally_offset) {
+      mci::set_error("problem %u: tally slots [%llu, +%llu) outside the tally (%llu slots)", i,
+                     (unsigned long long)q.tally_offset, (unsigned long long)slots,
+                     (unsigned long long)t->n_slots);
+      return MC_ERR_ARG;
+    }
+    acc += q.n_histories;
+  }
+  *total = acc;
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+MC_API const char* mc_last_error(void) { return mci::g_last_error.c_str(); }
+
+MC_API int mc_ctx_create(mc_ctx** out, int device) {
+  if (!out) {
+    mci::set_error("mc_ctx_create: out is NULL");
+    return MC_ERR_ARG;
+  }
+  *out = nullptr;
+  MC_TRY_CUDA(cudaSetDevice(device));
+  mc_ctx* c = new mc_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = (size_t)optin;
+  int st = c->scratch.reserve(kScratchBytes);
+  if (st != MC_OK) {
+    delete c;
+    return st;
+  }
+  st = mci::cuda_status(cudaMemset(c->scratch.ptr, 0, kScratchBytes), "cudaMemset(scratch)");
+  if (st != MC_OK) {
+    c->scratch.release();
+    delete c;
+    return st;
+  }
+  *out = c;
+  return MC_OK;
+}
+
+MC_API void mc_ctx_destroy(mc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->staged) cudaEventDestroy(ctx->staged);
+  ctx->scratch.release();
+  ctx->problems.release();
+  ctx->bank.release();
+  if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
+  delete ctx;
+}
+
+MC_API uint64_t mc_hash64(uint64_t k, uint64_t s) { return mcd::hash64(k, s); }
+
+MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
+                            uint32_t n_problems, const mc_run_config* cfg, const mc_tally* tally,
+                            void* stream) {
+  if (!ctx || !problems || n_problems == 0 || !cfg || !tally || !tally->d_bins || !tally->d_counts) {
+    mci::set_error("mc_transport_run: NULL argument or no problems");
+    return MC_ERR_ARG;
+  }
+  int st = mci::check_lcg(lcg);
+  if (st != MC_OK) return st;
+  uint64_t total = 0;
+  st = check_problems(problems, n_problems, tally, &total);
+  if (st != MC_OK) return st;
+  if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
+      (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512))) {
+    mci::set_error("mc_transport_run: bad run config (schedule/precision/tally_mode/block)");
+    return MC_ERR_ARG;
+  }
+  const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? total : cfg->range_end;
+  if (rb > re || re > total) {
+    mci::set_error("mc_transport_run: range [%llu, %llu) outside the %llu histories", (unsigned long long)rb,
+                   (unsigned long long)re, (unsigned long long)total);
+    return MC_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+
+  st = stage_problems(ctx, problems, n_problems, s);
+  if (st != MC_OK) return st;
+  if (!cfg->accumulate) {
+    MC_TRY_CUDA(cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), s));
+    MC_TRY_CUDA(cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), s));
+  }
+  auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
+  MC_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+  if (re == rb) return MC_OK;
+
+  mci::SlabLaunch L{};
+  L.d_probs = ctx->problems.ptr;
+  L.n_problems = n_problems;
+  L.chunk = cfg->chunk ? cfg->chunk : 128u;
+  L.range_begin = rb;
+  L.total = re - rb;
+  L.d_ticket = ticket;
+  L.tally = tally;
+  L.lcg = *lcg;
+  L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 40);
+  const uint64_t smem_cap = 8192;  // slots (64 KiB) staged in shared memory under "auto"
+  const bool fits = tally->n_slots * 8u <= ctx->smem_optin;
+  if (cfg->tally_mode == 1 && !fits) {
+    mci::set_error("mc_transport_run: %llu tally slots do not fit in shared memory",
+                   (unsigned long long)tally->n_slots);
+    return MC_ERR_ARG;
+  }
+  const bool stage = cfg->tally_mode == 1 || (cfg->tally_mode == 0 && tally->n_slots <= smem_cap);
+  L.smem_slots = stage ? (uint32_t)tally->n_slots : 0u;
+  L.f32 = cfg->precision == MC_FP32_GUARDED;
+  L.block = cfg->block ? (int)cfg->block : 256;
+  L.blocks_per_sm = (int)cfg->blocks_per_sm;
+  L.num_sms = ctx->num_sms;
+  return mci::slab_history_launch(L, s);
+}
+
+MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t problem, const mc_tally* tally,
+                         double* h_flux, double* h_rel_err, double* h_batch, int64_t* h_raw,
+                         uint64_t* h_counts, void* stream) {
+  if (!ctx || !problems || !tally || !tally->d_bins || !tally->d_counts || !h_flux) {
+    mci::set_error("mc_tally_read: NULL argument");
+    return MC_ERR_ARG;
+  }
+  const mc_problem& p = problems[problem];
+  const uint32_t nb = p.n_bins, nbat = p.n_batches;
+  const uint64_t slots = (uint64_t)nb * nbat;
+  if (nb == 0 || nbat == 0 || p.tally_offset > tally->n_slots || slots > tally->n_slots - p.tally_offset) {
+    mci::set_error("mc_tally_read: problem %u does not fit the tally", problem);
+    return MC_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+  std::vector<int64_t> raw(slots);
+  std::vector<uint64_t> cnt(MC_NCOUNT);
+  MC_TRY_CUDA(cudaMemcpyAsync(raw.data(), tally->d_bins + p.tally_offset, slots * sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
+  MC_TRY_CUDA(cudaMemcpyAsync(cnt.data(), tally->d_counts + (size_t)problem * MC_NCOUNT,
+                              MC_NCOUNT * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  MC_TRY_CUDA(cudaStreamSynchronize(s));
+  if (h_raw) std::memcpy(h_raw, raw.data(), slots * sizeof(int64_t));
+  if (h_counts) std::memcpy(h_counts, cnt.data(), MC_NCOUNT * sizeof(uint64_t));
+
+  // Cell volume per bin: slab width L/n_bins.
+  const double vol = p.L / (double)nb;
+  const double scale = std::ldexp(1.0, -32);
+  const uint64_t N = p.n_histories;
+  bool overflow = false;
+  std::vector<double> total(nb, 0.0);
+  std::vector<double> batch(slots, 0.0);
+  for (uint32_t k = 0; k < nbat; ++k) {
+    // Batch k holds the ids with floor(id * nbat / N) == k.
+    const uint64_t lo = (uint64_t)(((unsigned __int128)k * N + nbat - 1) / nbat);
+    const uint64_t hi = (uint64_t)(((unsigned __int128)(k + 1) * N + nbat - 1) / nbat);
+    const double nk = (double)(hi - lo);
+    for (uint32_t b = 0; b < nb; ++b) {
+      const int64_t v = raw[(size_t)k * nb + b];
+      if (v >= (1ll << 62) || v <= -(1ll << 62)) overflow = true;
+      total[b] += (double)v;
+      batch[(size_t)k * nb + b] = nk > 0 ? (double)v * scale / (nk * vol) : 0.0;
+    }
+  }
+  for (uint32_t b = 0; b < nb; ++b) h_flux[b] = N > 0 ? total[b] * scale / ((double)N * vol) : 0.0;
+  if (h_batch) std::memcpy(h_batch, batch.data(), slots * sizeof(double));
+  if (h_rel_err) {
+    for (uint32_t b = 0; b < nb; ++b) {
+      if (nbat < 2 || h_flux[b] == 0.0) {
+        h_rel_err[b] = 0.0;
+        continue;
+      }
+      double mean = 0.0;
+      for (uint32_t k = 0; k < nbat; ++k) mean += batch[(size_t)k * nb + b];
+      mean /= nbat;
+      double var = 0.0;
+      for (uint32_t k = 0; k < nbat; ++k) {
+        const double d = batch[(size_t)k * nb + b] - mean;
+        var += d * d;
+      }
+      var /= (nbat - 1);
+      h_rel_err[b] = std::sqrt(var / nbat) / std::fabs(h_flux[b]);
+    }
+  }
+  if (overflow) {
+    mci::set_error("mc_tally_read: a bin of problem %u reached the int64 headroom 2^62", problem);
+    return MC_ERR_OVERFLOW;
+  }
+  if (cnt[MC_C_CAPPED] != 0) {
+    mci::set_error("mc_tally_read: %llu histories of problem %u hit the event cap",
+                   (unsigned long long)cnt[MC_C_CAPPED], problem);
+    return MC_ERR_EVENT_CAP;
+  }
+  return MC_OK;
+}
+
+}  // extern "C"

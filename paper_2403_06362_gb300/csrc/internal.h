@@ -1,0 +1,56 @@
+// internal.h -- shared host-side plumbing of libmc (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/mc.h"
+
+namespace mci {
+
+// Thread-local message of the last failing call (returned by mc_last_error).
+void set_error(const char* fmt, ...);
+
+// Returns MC_ERR_CUDA with a message if `e` is an error, else MC_OK.
+int cuda_status(cudaError_t e, const char* what);
+
+#define MC_TRY_CUDA(expr)                                   \
+  do {                                                      \
+    int _st = ::mci::cuda_status((expr), #expr);            \
+    if (_st != MC_OK) return _st;                           \
+  } while (0)
+
+// Validates an mc_lcg; fills `m`, `mask`.  Returns MC_OK or MC_ERR_ARG.
+int check_lcg(const mc_lcg* lcg);
+
+// Device scratch owned by a context.  Sizes only grow, and only outside
+// the launch of a run (never inside a captured region).
+struct DeviceBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  int reserve(size_t want);  // grows with cudaMalloc; contents not kept
+  void release();
+};
+
+struct GraphCache;  // transport launch graphs keyed by shape
+
+}  // namespace mci
+
+struct mc_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;  // max dynamic shared memory per block (opt-in)
+  // Small scratch: work tickets, status word, count staging.
+  mci::DeviceBuf scratch;
+  // Device copy of the problem list and per-problem derived constants.
+  mci::DeviceBuf problems;
+  // Pinned host staging of the problem list (uploaded with cudaMemcpyAsync).
+  void* h_problems = nullptr;
+  size_t h_problems_bytes = 0;
+  cudaEvent_t staged = nullptr;  // recorded after the last upload from h_problems
+  // Event-based schedule: particle banks.
+  mci::DeviceBuf bank;
+  mci::GraphCache* graphs = nullptr;
+};

@@ -1,0 +1,136 @@
+// mc_device.cuh -- device-side LCG, skip-ahead, hash and uniform conversion.
+//
+// Everything here is integer arithmetic that the GB300 SM runs on its
+// integer pipes: a 64-bit product is one IMAD.WIDE.U32 plus two IMADs, and
+// the fp64 uniform is assembled from integer pieces (clz, funnel shift,
+// exponent add) so that no fp64 instruction is issued on the draw path
+// (fp64 is a narrow unit on this part).
+#pragma once
+#include <cstdint>
+
+namespace mcd {
+
+// Listing 1 multiplier of the modified murmur_hash64a.
+constexpr uint64_t kMurmurM = 0xC6A4A7935BD1E995ull;
+
+// Parameters of Eq. (1) as the kernels use them.  The recurrence runs mod
+// 2^64 in registers; reduction mod 2^m is a ring homomorphism from Z/2^64,
+// so the low m bits of the 64-bit state are the m-bit state, and the mask
+// is applied only where a state leaves the kernel.
+struct Lcg {
+  uint64_t g, c, mask;
+  uint32_t m;
+};
+
+__host__ __device__ __forceinline__ uint64_t mask_of(uint32_t m) {
+  return m >= 64 ? ~0ull : ((1ull << m) - 1ull);
+}
+
+__device__ __forceinline__ uint64_t lcg_step(uint64_t x, uint64_t g, uint64_t c) {
+  return g * x + c;  // wraps mod 2^64
+}
+
+// Affine map x -> a*x + b (mod 2^64): the map of some number of LCG steps.
+struct Affine {
+  uint64_t a, b;
+};
+
+__host__ __device__ __forceinline__ Affine compose(Affine outer, Affine inner) {
+  // outer(inner(x)) = oa*(ia*x + ib) + ob
+  return Affine{outer.a * inner.a, outer.a * inner.b + outer.b};
+}
+
+__host__ __device__ __forceinline__ uint64_t apply(Affine f, uint64_t x) { return f.a * x + f.b; }
+
+// Eq. (2), Brown's binary method: the map of k steps from the map of one
+// step, by squaring (map of 2^(j+1) steps = map of 2^j steps applied twice)
+// and composing the squares selected by the bits of k.
+__host__ __device__ __forceinline__ Affine skip_map(uint64_t g, uint64_t c, uint64_t k) {
+  Affine acc{1ull, 0ull};
+  Affine sq{g, c};
+  while (k) {
+    if (k & 1ull) acc = compose(sq, acc);
+    sq = compose(sq, sq);
+    k >>= 1;
+  }
+  return acc;
+}
+
+// Listing 1: subhash(x) = (xM) ^ ((xM) >> 47);
+// hash(k, s) = subhash(subhash(s ^ 8M) ^ (subhash(k) * M)).
+__host__ __device__ __forceinline__ uint64_t subhash(uint64_t x) {
+  const uint64_t t = x * kMurmurM;
+  return t ^ (t >> 47);
+}
+
+// The seed half of the hash, computed once per parent seed.
+__host__ __device__ __forceinline__ uint64_t seed_hash_of(uint64_t s) {
+  return subhash(s ^ (8ull * kMurmurM));
+}
+
+__host__ __device__ __forceinline__ uint64_t hash_with(uint64_t k, uint64_t seed_hash) {
+  return subhash(seed_hash ^ (subhash(k) * kMurmurM));
+}
+
+__host__ __device__ __forceinline__ uint64_t hash64(uint64_t k, uint64_t s) {
+  return hash_with(k, seed_hash_of(s));
+}
+
+// Exact conversion of an integer n < 2^53 to the double n * 2^-53, built
+// from integer operations: normalise n so that its top bit sits at bit 52,
+// then add the biased exponent one below the true one (the leading 1 at bit
+// 52 carries into the exponent field).  For n in [2^52, 2^53) the value is
+// in [0.5, 1) with biased exponent 1022 = 1033 - clz64(n); in general the
+// word to add is (1032 - clz64(n)) << 52.
+__device__ __forceinline__ double u53_to_double(uint32_t hi, uint32_t lo) {
+  uint32_t rhi, rlo;
+  if (hi != 0u) {  // all but 2^-21 of the draws
+    const uint32_t lz = __clz(hi);  // 11..31 since hi < 2^21
+    const uint32_t s = lz - 11u;
+    rhi = __funnelshift_l(lo, hi, s) + ((1032u - lz) << 20);
+    rlo = lo << s;
+  } else if (lo != 0u) {
+    const uint32_t lz = 32u + __clz(lo);  // 32..63
+    const uint64_t nn = (uint64_t)lo << (lz - 11u);
+    const uint64_t bits = nn + ((uint64_t)(1032u - lz) << 52);
+    rhi = (uint32_t)(bits >> 32);
+    rlo = (uint32_t)bits;
+  } else {
+    rhi = 0u;
+    rlo = 0u;
+  }
+  return __hiloint2double((int)rhi, (int)rlo);
+}
+
+// Uniform of an (unmasked, mod 2^64) state for the common m = 63: bits
+// 10..62 of x, i.e. the top 53 of the 63 state bits.
+__device__ __forceinline__ double u01_m63(uint64_t x) {
+  const uint32_t xlo = (uint32_t)x, xhi = (uint32_t)(x >> 32);
+  const uint32_t lo = __funnelshift_r(xlo, xhi, 10);
+  const uint32_t hi = (xhi << 1) >> 11;
+  return u53_to_double(hi, lo);
+}
+
+// Uniform for any 1 <= m <= 64.
+__device__ __forceinline__ double u01_any(uint64_t x, uint32_t m) {
+  if (m >= 53u) {
+    const uint64_t n = (x & mask_of(m)) >> (m - 53u);
+    return u53_to_double((uint32_t)(n >> 32), (uint32_t)n);
+  }
+  // m < 53: x * 2^-m == (x << (53 - m)) * 2^-53, still below 2^53.
+  const uint64_t n = (x & mask_of(m)) << (53u - m);
+  return u53_to_double((uint32_t)(n >> 32), (uint32_t)n);
+}
+
+template <int M>
+__device__ __forceinline__ double u01(uint64_t x, uint32_t m) {
+  if constexpr (M == 63) {
+    return u01_m63(x);
+  } else {
+    return u01_any(x, m);
+  }
+}
+
+__device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
+
+}  // namespace mcd

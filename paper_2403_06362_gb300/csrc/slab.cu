@@ -1,0 +1,291 @@
+// slab.cu -- persistent history-based slab transport and the host side of
+// mc_transport_run.
+//
+// One lane carries one history at a time: its LCG state, position and
+// direction stay in registers.  Each loop iteration every live lane flies
+// one flight (and collides once); a lane whose history ended refills from
+// its warp's chunk of history indices, and the warp leader takes a new chunk
+// from a global ticket when the chunk runs dry.  So a warp keeps all 32
+// lanes busy until the ticket is exhausted, however uneven the histories.
+//
+// Tallies are int64 fixed point (2^32), staged in shared memory when the
+// whole tally fits and flushed with one global atomic per nonzero slot per
+// block; otherwise contributions go straight to global atomics.  Counters
+// are accumulated per lane and flushed when a lane changes problem.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "slab.cuh"
+#include "transport.h"
+
+namespace {
+
+using mcs::SlabDev;
+
+__global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    SlabDev& q = p[i];
+    q.h = q.L / (double)q.n_bins;
+    q.inv_h = (double)q.n_bins / q.L;
+    q.inv_st = 1.0 / q.sigma_t;
+    q.p_abs = 1.0 - q.c;
+    q.L_f = (float)q.L;
+    q.h_f = q.L_f / (float)q.n_bins;
+    q.inv_h_f = (float)q.n_bins / q.L_f;
+    q.inv_st_f = 1.0f / (float)q.sigma_t;
+    q.guard_f = q.L_f * 0x1p-18f;
+    const uint64_t parent = q.seeding == MC_SEED_HASH_HIER ? mcd::hash64(q.key, q.seed) : q.seed;
+    q.seed_hash = mcd::seed_hash_of(parent);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t acc = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      p[i].hist_begin = acc;
+      acc += p[i].n_hist;
+    }
+  }
+}
+
+struct RunArgs {
+  const SlabDev* probs;
+  uint32_t nprob;
+  uint32_t chunk;
+  uint64_t range_begin, total;
+  unsigned long long* ticket;
+  unsigned long long* tally;
+  unsigned long long* counts;
+  uint64_t* hist_state;
+  uint64_t* hist_draws;
+  mcd::Lcg lcg;
+  uint64_t event_cap;
+  uint32_t smem_slots;
+};
+
+// Per-lane counters for the lane's current problem.
+struct LaneCounts {
+  int prob;
+  uint32_t src, flights, coll, absn, scat, llo, lhi, capped, exh;
+  uint64_t draws, exd, maxd;
+  __device__ void clear() {
+    src = flights = coll = absn = scat = llo = lhi = capped = exh = 0u;
+    draws = exd = maxd = 0ull;
+  }
+  __device__ void flush(unsigned long long* counts) {
+    if (prob < 0) return;
+    unsigned long long* c = counts + (size_t)prob * MC_NCOUNT;
+    if (src) atomicAdd(c + MC_C_SOURCE, (unsigned long long)src);
+    if (flights) atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)flights);
+    if (coll) atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)coll);
+    if (absn) atomicAdd(c + MC_C_ABSORPTIONS, (unsigned long long)absn);
+    if (scat) atomicAdd(c + MC_C_SCATTERS, (unsigned long long)scat);
+    if (llo) atomicAdd(c + MC_C_LEAK_LO, (unsigned long long)llo);
+    if (lhi) atomicAdd(c + MC_C_LEAK_HI, (unsigned long long)lhi);
+    if (draws) atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
+    if (exh) atomicAdd(c + MC_C_EXCEED_HIST, (unsigned long long)exh);
+    if (exd) atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)exd);
+    if (capped) atomicAdd(c + MC_C_CAPPED, (unsigned long long)capped);
+    if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
+    clear();
+  }
+};
+
+__device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, uint64_t gi) {
+  uint32_t lo = 0, hi = n - 1;  // largest i with hist_begin <= gi
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (p[mid].hist_begin <= gi) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int M, bool F32, bool SMEM>
+__global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
+  extern __shared__ unsigned long long s_tally[];
+  __shared__ mcd::Affine tab[64];
+  if (threadIdx.x == 0) {
+    mcd::Affine sq{a.lcg.g, a.lcg.c};
+    for (int j = 0; j < 64; ++j) { tab[j] = sq; sq = mcd::compose(sq, sq); }
+  }
+  if constexpr (SMEM) {
+    for (uint32_t s = threadIdx.x; s < a.smem_slots; s += blockDim.x) s_tally[s] = 0ull;
+  }
+  __syncthreads();
+
+  const unsigned kFull = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const mcd::Lcg l = a.lcg;
+
+  uint64_t pool_next = 0, pool_end = 0;
+  bool more = true;
+  bool alive = false;
+  LaneCounts lc;
+  lc.prob = -1;
+  lc.clear();
+
+  const SlabDev* P = a.probs;
+  mcs::Rng<M> r{0ull, 0ull};
+  mcs::SlabParticle q{};
+  mcs::Sink sink{nullptr};
+  uint64_t gi = 0, events = 0;
+
+  for (;;) {
+    unsigned dead = __ballot_sync(kFull, !alive);
+    while (dead != 0u && more) {
+      if (pool_next >= pool_end) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.ticket, (unsigned long long)a.chunk);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= a.total) { more = false; break; }
+        pool_next = base;
+        pool_end = min((uint64_t)base + (uint64_t)a.chunk, (uint64_t)a.total);
+      }
+      const uint64_t avail = pool_end - pool_next;
+      const unsigned rank = __popc(dead & lt_mask);
+      if (!alive && rank < avail) {
+        gi = a.range_begin + pool_next + rank;
+        const uint32_t pi = a.nprob == 1 ? 0u : find_problem(a.probs, a.nprob, gi);
+        if ((int)pi != lc.prob) { lc.flush(a.counts); lc.prob = (int)pi; }
+        P = a.probs + pi;
+        const uint64_t id = gi - P->hist_begin;
+        const uint64_t batch = mcs::batch_of(id, P->n_hist, P->n_batches);
+        sink.base = (SMEM ? s_tally : a.tally) + P->tally_offset + batch * P->n_bins;
+        r.x = mcs::slab_seed(*P, id, tab, l.mask);
+        r.draws = 0;
+        mcs::slab_source<M, F32>(*P, r, l, q);
+        events = 0;
+        ++lc.src;
+        alive = true;
+      }
+      pool_next += min((uint64_t)__popc(dead), avail);
+      dead = __ballot_sync(kFull, !alive);
+    }
+    if (__ballot_sync(kFull, alive) == 0u) break;
+    if (alive) {
+      int outcome;
+      if (events == a.event_cap) {
+        ++lc.capped;
+        outcome = -1;
+      } else {
+        ++events;
+        ++lc.flights;
+        outcome = mcs::slab_event<M, F32>(*P, r, l, q, sink, lc.coll, lc.scat);
+        if (outcome == mcs::kAbsorbed) ++lc.absn;
+        else if (outcome == mcs::kLeakLo) ++lc.llo;
+        else if (outcome == mcs::kLeakHi) ++lc.lhi;
+      }
+      if (outcome != mcs::kContinue) {
+        lc.draws += r.draws;
+        if (r.draws > lc.maxd) lc.maxd = r.draws;
+        if (P->stride_q != 0 && r.draws > P->stride_q) { ++lc.exh; lc.exd += r.draws - P->stride_q; }
+        if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
+        if (a.hist_draws) a.hist_draws[gi] = r.draws;
+        alive = false;
+        if (lc.draws > (1ull << 31)) lc.flush(a.counts);
+      }
+    }
+  }
+  lc.flush(a.counts);
+
+  if constexpr (SMEM) {
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < a.smem_slots; s += blockDim.x) {
+      const unsigned long long v = s_tally[s];
+      if (v != 0ull) atomicAdd(a.tally + s, v);
+    }
+  }
+}
+
+template <int M, bool F32, bool SMEM>
+int launch_history(const RunArgs& a, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
+  auto k = slab_history_kernel<M, F32, SMEM>;
+  const size_t smem = SMEM ? (size_t)a.smem_slots * 8u : 0u;
+  if (smem > 48u * 1024u) {
+    int st = mci::cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                              "cudaFuncSetAttribute(slab_history_kernel)");
+    if (st != MC_OK) return st;
+  }
+  int per_sm = blocks_per_sm;
+  if (per_sm <= 0) {
+    int st = mci::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem),
+                              "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (st != MC_OK) return st;
+    if (per_sm < 1) per_sm = 1;
+  }
+  // Enough warps for every chunk, never more than fill the GPU.
+  const uint64_t warps_needed = (a.total + a.chunk - 1) / a.chunk;
+  const uint64_t blocks_needed = (warps_needed * 32 + block - 1) / block;
+  const uint64_t full = (uint64_t)num_sms * (uint64_t)per_sm;
+  const int grid = (int)std::max<uint64_t>(1, std::min(full, blocks_needed));
+  k<<<grid, block, smem, s>>>(a);
+  return mci::cuda_status(cudaGetLastError(), "slab_history_kernel launch");
+}
+
+template <int M>
+int launch_history_m(const RunArgs& a, bool f32, int block, int bps, int sms, cudaStream_t s) {
+  const bool smem = a.smem_slots != 0;
+  if (f32) return smem ? launch_history<M, true, true>(a, block, bps, sms, s)
+                       : launch_history<M, true, false>(a, block, bps, sms, s);
+  return smem ? launch_history<M, false, true>(a, block, bps, sms, s)
+              : launch_history<M, false, false>(a, block, bps, sms, s);
+}
+
+}  // namespace
+
+namespace mci {
+
+size_t slab_dev_size() { return sizeof(SlabDev); }
+
+void slab_fill_host(const mc_problem* src, uint32_t n, void* dst) {
+  SlabDev* d = static_cast<SlabDev*>(dst);
+  for (uint32_t i = 0; i < n; ++i) {
+    SlabDev q;
+    std::memset(&q, 0, sizeof q);
+    q.L = src[i].L;
+    q.sigma_t = src[i].sigma_t;
+    q.c = src[i].c;
+    q.n_hist = src[i].n_histories;
+    q.seed = src[i].seed;
+    q.stride_q = src[i].stride_q;
+    q.id_offset = src[i].id_offset;
+    q.key = src[i].key;
+    q.tally_offset = src[i].tally_offset;
+    q.n_bins = src[i].n_bins;
+    q.n_batches = src[i].n_batches;
+    q.source = src[i].source;
+    q.seeding = src[i].seeding;
+    d[i] = q;
+  }
+}
+
+int slab_prep(void* d_probs, uint32_t n, cudaStream_t s) {
+  slab_prep_kernel<<<1, 256, 0, s>>>(static_cast<SlabDev*>(d_probs), n);
+  return cuda_status(cudaGetLastError(), "slab_prep_kernel launch");
+}
+
+int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
+  RunArgs a{};
+  a.probs = static_cast<const SlabDev*>(L.d_probs);
+  a.nprob = L.n_problems;
+  a.chunk = L.chunk;
+  a.range_begin = L.range_begin;
+  a.total = L.total;
+  a.ticket = L.d_ticket;
+  a.tally = reinterpret_cast<unsigned long long*>(L.tally->d_bins);
+  a.counts = reinterpret_cast<unsigned long long*>(L.tally->d_counts);
+  a.hist_state = L.tally->d_hist_state;
+  a.hist_draws = L.tally->d_hist_draws;
+  a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
+  a.event_cap = L.event_cap;
+  a.smem_slots = L.smem_slots;
+  if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+  return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+}
+
+}  // namespace mci

@@ -1,0 +1,241 @@
+// slab.cuh -- device view of a slab problem and the per-particle physics
+// shared by the history-based and the event-based slab schedules.
+//
+// Both schedules call the same functions below for every draw, flight,
+// collision and tally contribution, so they make the same int64 tally
+// contributions; int64 addition is associative, so the totals are
+// bit-identical whatever the order of the additions.
+//
+// fp64 path: every operation is the one the transport definition names,
+// rounded once (this file is compiled with --fmad=false, so no a*b+c is
+// contracted).  fp32 path: flight length and geometry in fp32, with an fp64
+// recomputation of the leak/collide decision when the fp32 end point lands
+// within a guard band of a slab face; uniforms, absorption tests and the
+// fixed-point scaling of tally contributions stay exact (fp64 or integer).
+#pragma once
+#include <cstdint>
+
+#include "../../include/mc.h"
+#include "mc_device.cuh"
+
+namespace mcs {
+
+struct SlabDev {
+  double L, sigma_t, c;
+  uint64_t n_hist, seed, stride_q, id_offset, key, tally_offset;
+  uint32_t n_bins, n_batches, source, seeding;
+  // derived on the device by the prep kernel
+  double h;             // bin width L / n_bins
+  double inv_h;         // n_bins / L: candidate-bin lookup only
+  double inv_st;        // 1 / sigma_t
+  double p_abs;         // 1 - c
+  float guard_f;        // fp32 path: half-width of the fp64 guard band at a face
+  float L_f, h_f, inv_h_f, inv_st_f;
+  uint64_t seed_hash;   // hash seeding: seed half of hash(., s) or of hash(., hash(key, s))
+  uint64_t hist_begin;  // global index of local history 0
+};
+
+constexpr double kFix = 4294967296.0;  // 2^32: fixed-point scale of the tallies
+
+// One LCG stream (Eq. 1) and its draw counter, held in registers.
+template <int M>
+struct Rng {
+  uint64_t x;
+  uint64_t draws;
+  __device__ __forceinline__ double next(const mcd::Lcg& l) {
+    x = mcd::lcg_step(x, l.g, l.c);
+    ++draws;
+    return mcd::u01<M>(x, l.m);
+  }
+};
+
+// The state k steps after x through a table of the maps of 2^j steps.
+__device__ __forceinline__ uint64_t skip_tab(const mcd::Affine* tab, uint64_t x, uint64_t k) {
+  while (k) {
+    const int j = __ffsll((long long)k) - 1;
+    x = mcd::apply(tab[j], x);
+    k &= k - 1;
+  }
+  return x;
+}
+
+// Seed of local history `id` (Eqs. 2-4): hash(id, s), hash(id, hash(key, s))
+// or X_{Q * (id_offset + id)}.
+__device__ __forceinline__ uint64_t slab_seed(const SlabDev& p, uint64_t id, const mcd::Affine* tab,
+                                              uint64_t mask) {
+  if (p.seeding == MC_SEED_STRIDE) return skip_tab(tab, p.seed, p.stride_q * (p.id_offset + id)) & mask;
+  return mcd::hash_with(id, p.seed_hash) & mask;
+}
+
+__device__ __forceinline__ uint64_t batch_of(uint64_t id, uint64_t n_hist, uint32_t n_batches) {
+  // floor(id * n_batches / n_hist) without 128-bit arithmetic when it fits.
+  if (id <= (~0ull) / (n_batches ? n_batches : 1)) return (id * n_batches) / n_hist;
+  const unsigned __int128 t = (unsigned __int128)id * n_batches;
+  return (uint64_t)(t / n_hist);
+}
+
+__device__ __forceinline__ double slab_edge(const SlabDev& p, int j) {
+  return j >= (int)p.n_bins ? p.L : (double)j * p.h;
+}
+
+__device__ __forceinline__ int clamp_bin(int j, int nb) { return j < 0 ? 0 : (j >= nb ? nb - 1 : j); }
+
+// Tally sink: shared-memory staging or direct global atomics.
+struct Sink {
+  unsigned long long* base;  // this history's [bin] row (smem or global)
+  __device__ __forceinline__ void add(int j, long long v) const {
+    if (v != 0) atomicAdd(base + j, (unsigned long long)v);
+  }
+};
+
+// Track length in every bin met by the segment [a, b] (a <= b) travelled
+// with 1/|mu| = w_mu: |[a,b] & [e_j, e_{j+1}]| * w_mu, to fixed point.
+__device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, double w_mu, const Sink& s) {
+  const int nb = (int)p.n_bins;
+  const int j0 = clamp_bin((int)(a * p.inv_h) - 1, nb);
+  const int j1 = clamp_bin((int)(b * p.inv_h) + 1, nb);
+  for (int j = j0; j <= j1; ++j) {
+    const double lo_e = slab_edge(p, j), hi_e = slab_edge(p, j + 1);
+    const double lo = a > lo_e ? a : lo_e;
+    const double hi = b < hi_e ? b : hi_e;
+    if (hi > lo) s.add(j, __double2ll_rn(__dmul_rn(__dmul_rn(__dsub_rn(hi, lo), w_mu), kFix)));
+  }
+}
+
+// mu == 0: the whole flight d lies in the bin holding x.
+__device__ __forceinline__ void point64(const SlabDev& p, double x, double d, const Sink& s) {
+  const int nb = (int)p.n_bins;
+  int j = clamp_bin((int)(x * p.inv_h), nb);
+  while (j > 0 && x < slab_edge(p, j)) --j;
+  while (j + 1 < nb && x >= slab_edge(p, j + 1)) ++j;
+  s.add(j, __double2ll_rn(__dmul_rn(d, kFix)));
+}
+
+// Exact llrint((double)v * 2^32) for a finite float v >= 0, in integer
+// arithmetic (scaling by 2^32 is exact; only values below 2^-9 need a
+// rounding of the shifted-out bits, done half-to-even).
+__device__ __forceinline__ long long fix32_from_float(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int e = (int)(b >> 23) & 0xff;
+  if (e == 0) return 0;  // zero or subnormal: below 2^-126, rounds to 0 at scale 2^32
+  const uint64_t mant = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 127 - 23 + 32;  // value * 2^32 = mant * 2^sh
+  if (sh >= 0) return (long long)(mant << sh);
+  if (sh < -25) return 0;
+  const int r = -sh;
+  const uint64_t q = mant >> r, rem = mant & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+  const uint64_t up = (rem > half) || (rem == half && (q & 1ull));
+  return (long long)(q + up);
+}
+
+__device__ __forceinline__ float slab_edge_f(const SlabDev& p, int j) {
+  return j >= (int)p.n_bins ? p.L_f : (float)j * p.h_f;
+}
+
+__device__ __forceinline__ void seg32(const SlabDev& p, float a, float b, float w_mu, const Sink& s) {
+  const int nb = (int)p.n_bins;
+  const int j0 = clamp_bin((int)(a * p.inv_h_f) - 1, nb);
+  const int j1 = clamp_bin((int)(b * p.inv_h_f) + 1, nb);
+  for (int j = j0; j <= j1; ++j) {
+    const float lo_e = slab_edge_f(p, j), hi_e = slab_edge_f(p, j + 1);
+    const float lo = fmaxf(a, lo_e), hi = fminf(b, hi_e);
+    if (hi > lo) s.add(j, fix32_from_float((hi - lo) * w_mu));
+  }
+}
+
+__device__ __forceinline__ void point32(const SlabDev& p, float x, float d, const Sink& s) {
+  const int nb = (int)p.n_bins;
+  int j = clamp_bin((int)(x * p.inv_h_f), nb);
+  while (j > 0 && x < slab_edge_f(p, j)) --j;
+  while (j + 1 < nb && x >= slab_edge_f(p, j + 1)) ++j;
+  s.add(j, fix32_from_float(d));
+}
+
+// Particle state of the slab physics.  fp64 path uses x, mu, w_mu; the
+// fp32 path keeps its geometry in xf, muf, wf.
+struct SlabParticle {
+  double x, mu, w_mu;
+  float xf, muf, wf;
+};
+
+// Outcome of one flight (+ collision).
+enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3 };
+
+// Source of a history (isotropic uniform in [0, L], or a beam at x = 0).
+template <int M, bool F32>
+__device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
+  if (p.source == MC_SRC_BEAM) {
+    q.x = 0.0; q.mu = 1.0; q.w_mu = 1.0;
+    q.xf = 0.0f; q.muf = 1.0f; q.wf = 1.0f;
+    return;
+  }
+  const double u1 = r.next(l);
+  const double u2 = r.next(l);
+  if constexpr (!F32) {
+    q.x = __dmul_rn(p.L, u1);
+    q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
+    q.w_mu = q.mu != 0.0 ? __ddiv_rn(1.0, fabs(q.mu)) : 0.0;
+  } else {
+    q.xf = p.L_f * (float)u1;
+    q.muf = 2.0f * (float)u2 - 1.0f;
+    q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
+  }
+}
+
+// One flight and, if the particle stays in the slab, one collision.
+// Counters: *coll and *scat are incremented here; the caller counts the
+// flight and the outcome.
+template <int M, bool F32>
+__device__ __forceinline__ int slab_event(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q,
+                                          const Sink& s, uint32_t& coll, uint32_t& scat) {
+  const double u = r.next(l);
+  if constexpr (!F32) {
+    const double d = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
+    const double xn = __dadd_rn(q.x, __dmul_rn(d, q.mu));
+    if (q.mu > 0.0 && xn >= p.L) { seg64(p, q.x, p.L, q.w_mu, s); return kLeakHi; }
+    if (q.mu < 0.0 && xn <= 0.0) { seg64(p, 0.0, q.x, q.w_mu, s); return kLeakLo; }
+    if (q.mu == 0.0) point64(p, q.x, d, s);
+    else if (q.mu > 0.0) seg64(p, q.x, xn, q.w_mu, s);
+    else seg64(p, xn, q.x, q.w_mu, s);
+    q.x = xn;
+  } else {
+    const float d = -log1pf(-(float)u) * p.inv_st_f;
+    float xn = fmaf(d, q.muf, q.xf);
+    // Guard band: re-decide leak vs collide in fp64 near a face.
+    const bool near_hi = q.muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
+    const bool near_lo = q.muf < 0.0f && fabsf(xn) <= p.guard_f;
+    bool leak_hi = q.muf > 0.0f && xn >= p.L_f, leak_lo = q.muf < 0.0f && xn <= 0.0f;
+    if (near_hi || near_lo) {
+      const double d64 = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
+      const double xn64 = __dadd_rn((double)q.xf, __dmul_rn(d64, (double)q.muf));
+      leak_hi = q.muf > 0.0f && xn64 >= p.L;
+      leak_lo = q.muf < 0.0f && xn64 <= 0.0;
+      xn = (float)xn64;
+      if (!leak_hi && !leak_lo) {
+        // keep the collision site strictly inside after rounding to fp32
+        if (xn >= p.L_f) xn = __int_as_float(__float_as_int(p.L_f) - 1);
+        if (xn <= 0.0f) xn = 1.0e-30f;
+      }
+    }
+    if (leak_hi) { seg32(p, q.xf, p.L_f, q.wf, s); return kLeakHi; }
+    if (leak_lo) { seg32(p, 0.0f, q.xf, q.wf, s); return kLeakLo; }
+    if (q.muf == 0.0f) point32(p, q.xf, d, s);
+    else if (q.muf > 0.0f) seg32(p, q.xf, xn, q.wf, s);
+    else seg32(p, xn, q.xf, q.wf, s);
+    q.xf = xn;
+  }
+  ++coll;
+  if (r.next(l) < p.p_abs) return kAbsorbed;
+  ++scat;
+  const double u2 = r.next(l);
+  if constexpr (!F32) {
+    q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
+    q.w_mu = q.mu != 0.0 ? __ddiv_rn(1.0, fabs(q.mu)) : 0.0;
+  } else {
+    q.muf = 2.0f * (float)u2 - 1.0f;
+    q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
+  }
+  return kContinue;
+}
+
+}  // namespace mcs

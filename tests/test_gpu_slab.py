@@ -1,0 +1,184 @@
+"""GPU parity of the slab transport (mc_transport_run / mc_tally_read)
+against the oracle: per-history final RNG state and draw count bit-exact,
+integer counters exact, int64 tallies within 1e-6 relative (fp64 path), and
+tally bits identical across launch shapes, staging modes and id ranges."""
+import numpy as np
+import pytest
+
+from paper_2403_06362_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+M, G, CC, Q = W.LCG_M, W.LCG_G, W.LCG_C, W.STRIDE_Q
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    ctx = mc.Context(0)
+    yield mc, ctx, torch
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def olcg(oracle):
+    return oracle.Lcg(m=M, pad=0, g=G, c=CC)
+
+
+def gpu_run(env, probs, n_hist_out=True, **cfg_kw):
+    mc, ctx, torch = env
+    total = sum(p["n_histories"] for p in probs)
+    tally = mc.Tally(W.tally_slots(probs), len(probs), n_histories=total if n_hist_out else 0)
+    cprobs = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    cfg = mc.mc_run_config(**cfg_kw)
+    mc.mc_transport_run(ctx, mc.make_lcg(), cprobs, cfg, tally.c)
+    torch.cuda.synchronize()
+    return tally, cprobs
+
+
+def oracle_run(oracle, probs, per_history=True):
+    size = W.tally_slots(probs)
+    tally = np.zeros(size, dtype=np.int64)
+    tf = np.zeros(size)
+    counts, hs, hd = [], [], []
+    for p in probs:
+        c = np.zeros(oracle.NCOUNT, dtype=np.uint64)
+        r = oracle.slab_run(olcg(oracle), W.to_oracle_problem(p, oracle), tally=tally, tally_fp=tf,
+                            counts=c, per_history=per_history)
+        counts.append(c)
+        if per_history:
+            hs.append(r["hist_state"])
+            hd.append(r["hist_draws"])
+    out = dict(tally=tally, tally_fp=tf, counts=np.array(counts))
+    if per_history:
+        out["hist_state"] = np.concatenate(hs)
+        out["hist_draws"] = np.concatenate(hd)
+    return out
+
+
+def assert_tally_close(got, exp):
+    got = np.asarray(got, dtype=np.int64)
+    exp = np.asarray(exp, dtype=np.int64)
+    diff = np.abs(got.astype(np.float64) - exp.astype(np.float64))
+    assert np.all(diff <= TOL * np.abs(exp.astype(np.float64))), (np.max(diff), np.argmax(diff))
+
+
+def counts_of(tally, n):
+    return tally.counts.cpu().numpy().view(np.uint64).reshape(n, 16)
+
+
+@pytest.mark.parametrize("seeding", [W.SEED_HASH, W.SEED_STRIDE, W.SEED_HASH_HIER])
+def test_slab_small_parity(env, oracle, seeding):
+    probs = W.slab_small(seeding)
+    tally, cprobs = gpu_run(env, probs)
+    o = oracle_run(oracle, probs)
+    assert np.array_equal(tally.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(tally.hist_draws.cpu().numpy().view(np.uint64), o["hist_draws"])
+    assert np.array_equal(counts_of(tally, 1)[:, :14], o["counts"][:, :14])
+    assert_tally_close(tally.bins.cpu().numpy(), o["tally"])
+    mc = env[0]
+    r = mc.mc_tally_read(env[1], cprobs, 0, tally.c)
+    h = probs[0]["L"] / probs[0]["n_bins"]
+    exp_flux = o["tally"].reshape(10, 20).sum(0) * 2.0**-32 / (probs[0]["n_histories"] * h)
+    assert np.allclose(r.flux, exp_flux, rtol=1e-6, atol=0)
+    assert r.counts["source"] == probs[0]["n_histories"]
+
+
+@pytest.mark.parametrize("block,chunk,mode", [(64, 1, 1), (128, 7, 2), (256, 128, 0), (512, 4096, 1),
+                                              (32, 32, 2)])
+def test_tally_bits_independent_of_launch_shape(env, oracle, block, chunk, mode):
+    probs = W.slab_small(W.SEED_HASH, n_histories=20_000)
+    base, _ = gpu_run(env, probs, n_hist_out=False)
+    t, _ = gpu_run(env, probs, n_hist_out=False, block=block, chunk=chunk, tally_mode=mode)
+    assert np.array_equal(t.bins.cpu().numpy(), base.bins.cpu().numpy())
+    assert np.array_equal(counts_of(t, 1), counts_of(base, 1))
+
+
+def test_ranges_accumulate_to_the_same_bits(env):
+    mc, ctx, torch = env
+    probs = W.slab_small(W.SEED_STRIDE, n_histories=20_000)
+    base, cprobs = gpu_run(env, probs, n_hist_out=False)
+    tally = mc.Tally(W.tally_slots(probs), 1)
+    for i, (a, b) in enumerate([(0, 1), (1, 7001), (7001, 19999), (19999, 20000)]):
+        cfg = mc.mc_run_config(range_begin=a, range_end=b, accumulate=1 if i else 0)
+        mc.mc_transport_run(ctx, mc.make_lcg(), cprobs, cfg, tally.c)
+    torch.cuda.synchronize()
+    assert np.array_equal(tally.bins.cpu().numpy(), base.bins.cpu().numpy())
+    c1, c0 = counts_of(tally, 1), counts_of(base, 1)
+    assert np.array_equal(c1[:, :13], c0[:, :13])
+
+
+def test_pure_absorber_beam_closed_form_on_gpu(env):
+    mc, ctx, torch = env
+    S, L, nb = 1.0, 4.0, 8
+    p = W.slab_problem(L, S, 0.0, 1_000_000, nb, 20, W.SEED_HASH, source=W.SRC_BEAM)
+    tally, cprobs = gpu_run(env, [p], n_hist_out=False)
+    r = mc.mc_tally_read(ctx, cprobs, 0, tally.c)
+    e = np.linspace(0, L, nb + 1)
+    exact = (np.exp(-S * e[:-1]) - np.exp(-S * e[1:])) / (S * (e[1:] - e[:-1]))
+    assert np.all(np.abs(r.flux - exact) < 4.5 * r.rel_err * r.flux)
+
+
+def test_batched_problems_parity(env, oracle):
+    # uneven problems in one launch; histories capped so the oracle is quick
+    probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=24, max_histories=3000)
+    tally, _ = gpu_run(env, probs)
+    o = oracle_run(oracle, probs)
+    assert np.array_equal(tally.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(counts_of(tally, len(probs))[:, :14], o["counts"][:, :14])
+    assert_tally_close(tally.bins.cpu().numpy(), o["tally"])
+    probs = W.slab_batched(W.SEED_STRIDE, n_problems=24, max_histories=3000)
+    tally, _ = gpu_run(env, probs)
+    o = oracle_run(oracle, probs)
+    assert np.array_equal(tally.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert_tally_close(tally.bins.cpu().numpy(), o["tally"])
+
+
+def test_long_chains_full_size_sampled(env, oracle):
+    """10^6 histories of the 200 cm, c = 0.9999 slab (stride seeding), in the
+    default launch shape; 400 sampled histories rerun one by one in the
+    oracle must match in final state and draw count, and the stride
+    exceedance counters must agree with the per-history draw counts."""
+    probs = W.slab_long(W.SEED_STRIDE)
+    tally, _ = gpu_run(env, probs)
+    hs = tally.hist_state.cpu().numpy().view(np.uint64)
+    hd = tally.hist_draws.cpu().numpy().view(np.uint64)
+    rng = np.random.default_rng(1)
+    sample = np.unique(rng.integers(0, probs[0]["n_histories"], 400))
+    P = W.to_oracle_problem(probs[0], oracle)
+    for i in sample:
+        r = oracle.slab_run(olcg(oracle), P, int(i), int(i) + 1, per_history=True)
+        assert int(r["hist_state"][0]) == int(hs[i]) and int(r["hist_draws"][0]) == int(hd[i]), i
+    c = counts_of(tally, 1)[0]
+    d = hd.astype(np.int64)
+    assert int(c[8]) == int(np.sum(d > Q))
+    assert int(c[9]) == int(np.sum(np.maximum(d - Q, 0)))
+    assert int(c[7]) == int(d.sum()) and int(c[13]) == int(d.max())
+    assert int(c[0]) == int(c[3]) + int(c[5]) + int(c[6])
+
+
+def test_event_cap_reported(env):
+    mc, ctx, torch = env
+    p = W.slab_problem(200.0, 1.0, 0.9999, 500, 10, 1, W.SEED_HASH)
+    tally, cprobs = gpu_run(env, [p], n_hist_out=False, event_cap=50)
+    r = mc.mc_tally_read(ctx, cprobs, 0, tally.c, check=False)
+    assert r.status == mc._ffi.MC_ERR_EVENT_CAP and r.counts["capped"] > 0
+
+
+def test_fp32_guarded_error_stated(env, oracle):
+    # fp32 flight: decisions may differ from fp64, so compare statistically
+    # and bound the per-bin relative deviation from the fp64 oracle.
+    probs = W.slab_small(W.SEED_HASH, n_histories=200_000)
+    probs[0]["n_batches"] = 20
+    t32, _ = gpu_run(env, probs, n_hist_out=False, precision=1)
+    o = oracle_run(oracle, probs, per_history=False)
+    g = t32.bins.cpu().numpy().reshape(20, 20).sum(0).astype(np.float64)
+    e = o["tally"].reshape(20, 20).sum(0).astype(np.float64)
+    rel = np.abs(g - e) / e
+    assert rel.max() < 2e-2, rel.max()
+    c32 = counts_of(t32, 1)[0]
+    assert int(c32[0]) == int(c32[3]) + int(c32[5]) + int(c32[6])
