@@ -218,6 +218,26 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
                             uint32_t n_problems, const mc_run_config* config, const mc_tally* tally,
                             void* stream);
 
+/* The slab transport of mc_transport_run for callers that cannot allocate
+ * device memory (the paper has no counterpart; this is a deployment aid).
+ * mc_transport_run needs an mc_ctx, and creating one calls cudaMalloc;
+ * code running under CUDA graph capture, code whose device memory belongs to
+ * another allocator, and code that must not grow its footprint after
+ * start-up cannot make that call.  This entry point allocates nothing: its
+ * scratch (work ticket and device problem list) is one fixed __device__
+ * array inside libmc, present on every device that loads the library until
+ * the process exits.
+ *   - At most 256 problems per call (MC_ERR_ARG beyond that); the
+ *     history-based schedule only (MC_SCHED_EVENT is MC_ERR_ARG).
+ *   - Same arguments, results and errors as mc_transport_run otherwise; the
+ *     caller still owns and passes the tally buffers.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make it before any stream capture starts.
+ *   - All calls share the array: calls whose GPU work overlaps (other
+ *     streams, other host threads) race and must be serialised. */
+MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                                   const mc_run_config* config, const mc_tally* tally, void* stream);
+
 /* Reads problem `problem`'s tally back (synchronises `stream`).
  *   h_flux      double[n_bins]: flux per source history and unit volume,
  *               phi_b = sum_b * 2^-32 / (N * V_b), over all batches.

@@ -122,6 +122,14 @@ def mc_transport_run(ctx, lcg, problems, config, tally, stream=None):
                                            C.byref(tally), _stream(stream)))
 
 
+def mc_transport_run_static(lcg, problems, config, tally, stream=None):
+    """mc_transport_run without a context: scratch lives in a fixed device
+    array inside libmc (for callers that cannot allocate device memory)."""
+    arr = problems if isinstance(problems, C.Array) else problem_array(problems)
+    return _ffi.check(lib().mc_transport_run_static(C.byref(lcg), arr, len(arr), C.byref(config),
+                                                    C.byref(tally), _stream(stream)))
+
+
 @dataclass
 class TallyRead:
     status: int

@@ -1,0 +1,59 @@
+"""mc_transport_run_static, the entry point for callers that cannot allocate
+device memory (no mc_ctx, scratch in a fixed device array inside libmc),
+must give the same results as mc_transport_run, call after call, even
+though every call reuses the array the previous call left behind.  This file
+is collected last so that a run stopping at the first failure has run every
+other test first."""
+import numpy as np
+import pytest
+
+from paper_2403_06362_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-6
+
+
+def run_both(mc, ctx, torch, probs):
+    lcg = mc.make_lcg()
+    total = sum(p["n_histories"] for p in probs)
+    arr = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    cfg = mc.mc_run_config()
+    ref = mc.Tally(W.tally_slots(probs), len(probs), n_histories=total)
+    mc.mc_transport_run(ctx, lcg, arr, cfg, ref.c)
+    got = mc.Tally(W.tally_slots(probs), len(probs), n_histories=total)
+    mc.mc_transport_run_static(lcg, arr, cfg, got.c)
+    torch.cuda.synchronize()
+    return ref, got
+
+
+def test_static_entry_matches_context_entry_on_consecutive_calls():
+    import torch
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    ctx = mc.Context(0)
+    # two different calls in a row: the second sees what the first left in
+    # the shared array (more problems, a nonzero ticket)
+    for probs in (W.slab_batched(W.SEED_HASH_HIER, n_problems=40, max_histories=5000),
+                  W.slab_small(W.SEED_STRIDE)):
+        ref, got = run_both(mc, ctx, torch, probs)
+        rb = ref.bins.cpu().numpy().astype(np.float64)
+        gb = got.bins.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gb - rb) <= TOL * np.abs(rb))
+        assert torch.equal(got.counts, ref.counts)
+        assert torch.equal(got.hist_state, ref.hist_state)
+        assert torch.equal(got.hist_draws, ref.hist_draws)
+    ctx.close()
+
+
+def test_static_entry_rejects_too_many_problems():
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=257, max_histories=10)
+    tally = mc.Tally(W.tally_slots(probs), len(probs))
+    arr = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    with pytest.raises(mc.McError) as e:
+        mc.mc_transport_run_static(mc.make_lcg(), arr, mc.mc_run_config(), tally.c)
+    assert e.value.status == mc._ffi.MC_ERR_ARG and "256" in str(e.value)
