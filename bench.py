@@ -36,11 +36,17 @@ METRIC = ("particle histories/sec and RNG draws/sec on 1 GB300 "
           "(hash vs stride, % int-pipe roofline)")
 N_STREAMS = 2**26
 DRAWS = 64
-# Integer instructions per draw of the formulation in csrc/mc_device.cuh:
-# 64-bit multiply-add as IMAD.WIDE + 2 IMAD (3); extraction of the top 53 of
-# 63 state bits (2); exact integer-to-fp64 assembly: nonzero test, clz,
-# shift amount, funnel shift, shift, exponent, add (7); 64-bit digest add (2).
+# Integer operations per draw of the formulation in csrc/mc_device.cuh
+# (u01_m63_bits_fast): 64-bit multiply-add as IMAD.WIDE + 2 IMAD with the
+# increment folded in (3); extraction of the top 53 of the 63 state bits:
+# funnel shift, shift, shift (3); exact integer-to-fp64 assembly: clz,
+# funnel shift, shift, exponent multiply-add, add (5); range flag for the
+# exact redo (1); 64-bit digest add (2).
 OPS_PER_DRAW = 14
+# DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
+# the ncu capture summarised in profiles/draw_digest_m63_kernel_rng_microbench.md
+# (mean of the hash and stride launches).  Set to None when the kernel changes.
+DRAW_KERNEL_TRAFFIC_BYTES = 1.0132e9
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 
@@ -289,9 +295,10 @@ def main():
     launch_ms = statistics.mean(t_hash + t_str)
     achieved = OPS_PER_DRAW * n * DRAWS / (launch_ms / 1e3)
     peak = int_issue_peak(props.multi_processor_count)
-    roofline = {"bound": "alu", "kernel": "draw_kernel (fused seed + 64 draws)",
+    roofline = {"bound": "alu", "kernel": "draw_digest_m63_kernel (fused seed + 64 draws, digest)",
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": DRAW_KERNEL_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (ncu dram read+write)",
                 "peak_note": f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {RECIPE_SM_MAX_MHZ:.0f} MHz",
                 "ops_per_draw": OPS_PER_DRAW}
 

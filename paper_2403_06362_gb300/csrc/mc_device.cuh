@@ -111,6 +111,23 @@ __device__ __forceinline__ double u01_m63(uint64_t x) {
   return u53_to_double(hi, lo);
 }
 
+// Branch-free form of u01_m63's bit pattern for the digest kernels: exact
+// whenever the top 21 of the 53 output bits are not all zero.  s_out > 20
+// flags the other case (probability 2^-21 per draw); the caller then redoes
+// the stream with u01_m63.  With t = (high word << 1), clz(t) is directly
+// the normalising shift s = clz(n) - 11 of the 53-bit integer n.
+__device__ __forceinline__ uint64_t u01_m63_bits_fast(uint64_t x, uint32_t& s_out) {
+  const uint32_t xlo = (uint32_t)x, xhi = (uint32_t)(x >> 32);
+  const uint32_t lo = __funnelshift_r(xlo, xhi, 10);
+  const uint32_t t = xhi << 1;
+  const uint32_t s = __clz(t);
+  const uint32_t hi = t >> 11;
+  const uint32_t rhi = __funnelshift_l(lo, hi, s) + ((1021u - s) << 20);
+  const uint32_t rlo = __funnelshift_l(0u, lo, s);
+  s_out = s;
+  return ((uint64_t)rhi << 32) | rlo;
+}
+
 // Uniform for any 1 <= m <= 64.
 __device__ __forceinline__ double u01_any(uint64_t x, uint32_t m) {
   if (m >= 53u) {

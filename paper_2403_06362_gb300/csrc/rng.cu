@@ -192,6 +192,107 @@ __global__ void __launch_bounds__(kDrawBlock) draw_kernel(const DrawArgs a) {
   }
 }
 
+// Digest-only draws for m = 63, the integer-issue-bound hot loop.  Each
+// thread carries two streams (i and i + T, T = threads in the grid) for
+// instruction-level parallelism; every uniform is built with the branch-free
+// u01_m63_bits_fast, and the rare stream that met a draw outside its range
+// is recomputed with the exact per-draw path.  DRAWS > 0 fixes the draw
+// count at compile time (fully unrolled); DRAWS = 0 reads it at run time.
+template <int SEED, int DRAWS>
+__global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawArgs a) {
+  __shared__ Affine tab[64];
+  if constexpr (SEED == kStride) build_pow2_table(tab, a.g, a.c);
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  if (tid >= a.n) return;
+  const uint32_t draws = DRAWS > 0 ? (uint32_t)DRAWS : a.draws;
+  Affine half{1ull, 0ull}, sweep{1ull, 0ull};
+  uint64_t xs = 0, seed_hash = 0;
+  if constexpr (SEED == kHash) seed_hash = mcd::seed_hash_of(a.hier ? mcd::hash64(a.key, a.seed) : a.seed);
+  if constexpr (SEED == kStride) {
+    half = map_by_table(tab, a.q * nthreads);
+    sweep = map_by_table(tab, a.q * 2ull * nthreads);
+    xs = skip_by_table(tab, a.x0, a.q * (a.id_begin + tid));
+  }
+  const uint64_t g = a.g, c = a.c;
+  for (uint64_t i = tid; i < a.n; i += 2 * nthreads) {
+    const uint64_t i2 = i + nthreads;
+    const bool two = i2 < a.n;
+    uint64_t x0a, x0b;
+    if constexpr (SEED == kLoad) {
+      x0a = a.states[i];
+      x0b = a.states[two ? i2 : i];
+    } else if constexpr (SEED == kHash) {
+      x0a = mcd::hash_with(a.id_begin + i, seed_hash) & a.mask;
+      x0b = mcd::hash_with(a.id_begin + (two ? i2 : i), seed_hash) & a.mask;
+    } else {
+      x0a = xs & a.mask;
+      x0b = mcd::apply(half, xs) & a.mask;
+      xs = mcd::apply(sweep, xs);
+    }
+    uint64_t xa = x0a, xb = x0b, da = 0, db = 0;
+    uint32_t sa = 0, sb = 0;
+    uint32_t j = 0;
+    if constexpr (DRAWS > 0) {
+#pragma unroll
+      for (int t = 0; t < DRAWS; ++t) {
+        uint32_t s1, s2;
+        xa = mcd::lcg_step(xa, g, c);
+        xb = mcd::lcg_step(xb, g, c);
+        da += mcd::u01_m63_bits_fast(xa, s1);
+        db += mcd::u01_m63_bits_fast(xb, s2);
+        sa = max(sa, s1);
+        sb = max(sb, s2);
+      }
+    } else {
+#pragma unroll 1
+      for (; j + 16 <= draws; j += 16) {
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          uint32_t s1, s2;
+          xa = mcd::lcg_step(xa, g, c);
+          xb = mcd::lcg_step(xb, g, c);
+          da += mcd::u01_m63_bits_fast(xa, s1);
+          db += mcd::u01_m63_bits_fast(xb, s2);
+          sa = max(sa, s1);
+          sb = max(sb, s2);
+        }
+      }
+      for (; j < draws; ++j) {
+        uint32_t s1, s2;
+        xa = mcd::lcg_step(xa, g, c);
+        xb = mcd::lcg_step(xb, g, c);
+        da += mcd::u01_m63_bits_fast(xa, s1);
+        db += mcd::u01_m63_bits_fast(xb, s2);
+        sa = max(sa, s1);
+        sb = max(sb, s2);
+      }
+    }
+    if (sa > 20u) {  // exact redo of stream a
+      xa = x0a;
+      da = 0;
+      for (uint32_t k = 0; k < draws; ++k) {
+        xa = mcd::lcg_step(xa, g, c);
+        da += mcd::dbits(mcd::u01_m63(xa));
+      }
+    }
+    if (sb > 20u) {
+      xb = x0b;
+      db = 0;
+      for (uint32_t k = 0; k < draws; ++k) {
+        xb = mcd::lcg_step(xb, g, c);
+        db += mcd::dbits(mcd::u01_m63(xb));
+      }
+    }
+    if (a.states) a.states[i] = xa & a.mask;
+    if (a.digest) a.digest[i] = da;
+    if (two) {
+      if (a.states) a.states[i2] = xb & a.mask;
+      if (a.digest) a.digest[i2] = db;
+    }
+  }
+}
+
 // Persistent grid: every SM filled to its occupancy limit, never more
 // blocks than the work needs.
 template <typename K>
@@ -207,6 +308,19 @@ int persistent_grid(K kernel, int block, size_t smem, uint64_t work_items) {
   uint64_t full = (uint64_t)cached_sms * per_sm;
   if (want < 1) want = 1;
   return (int)(want < full ? want : full);
+}
+
+template <int SEED>
+int launch_digest_m63(const DrawArgs& a, cudaStream_t s) {
+  const uint64_t work = (a.n + 1) / 2;
+  if (a.draws == 64) {
+    auto k = draw_digest_m63_kernel<SEED, 64>;
+    k<<<persistent_grid(k, kDrawBlock, 0, work), kDrawBlock, 0, s>>>(a);
+  } else {
+    auto k = draw_digest_m63_kernel<SEED, 0>;
+    k<<<persistent_grid(k, kDrawBlock, 0, work), kDrawBlock, 0, s>>>(a);
+  }
+  return mci::cuda_status(cudaGetLastError(), "draw_digest_m63_kernel launch");
 }
 
 template <int M, int SEED>
@@ -332,6 +446,14 @@ MC_API int mc_lcg_draw(mc_ctx* ctx, const mc_lcg* lcg, const mc_seed_spec* seed,
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (lcg->m == 63 && !d_u) {
+    // integer-issue-bound form: no uniforms stored, digest and/or final states
+    switch (mode) {
+      case kLoad: return launch_digest_m63<kLoad>(a, s);
+      case kHash: return launch_digest_m63<kHash>(a, s);
+      default: return launch_digest_m63<kStride>(a, s);
+    }
+  }
   if (lcg->m == 63) return launch_draw_m<63>(a, mode, s);
   return launch_draw_m<0>(a, mode, s);
 }

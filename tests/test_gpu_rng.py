@@ -169,3 +169,34 @@ def test_full_microbench_sampled(env, oracle):
         dg2 = torch.empty(n, dtype=torch.int64, device="cuda")
         mc.mc_lcg_draw(ctx, mc.make_lcg(), None, 0, seeds_dev, n, draws, None, dg2)
         assert torch.equal(dg, dg2) and torch.equal(st, seeds_dev)
+
+
+@pytest.mark.parametrize("draws", [0, 1, 2, 15, 16, 17, 63, 64, 65, 130])
+@pytest.mark.parametrize("n", [1, 2, 3, 1001, 65_537])
+def test_digest_only_kernel(env, oracle, draws, n):
+    # the integer-issue-bound form (no uniforms stored): two streams per
+    # thread, compile-time and run-time draw counts, odd stream counts
+    mc, ctx, torch = env
+    seeds = oracle.seed_hash(M, 7, 99, n)
+    v = torch.from_numpy(seeds.view(np.int64).copy()).cuda()
+    dg = torch.empty(n, dtype=torch.int64, device="cuda")
+    mc.mc_lcg_draw(ctx, mc.make_lcg(), None, 0, v, n, draws, None, dg)
+    o_st, _, o_dg = oracle.lcg_draw(M, G, CC, seeds, draws, want_u=False)
+    assert np.array_equal(u64(v), o_st)
+    assert np.array_equal(u64(dg), o_dg)
+
+
+@pytest.mark.parametrize("draws", [5, 64])
+def test_digest_kernel_rare_conversion_path(env, oracle, draws):
+    # first states whose top 21 output bits are zero force the exact redo
+    mc, ctx, torch = env
+    special = np.array([0, 1, 1023, 1024, 2**32, 2**42 - 1, 2**42, 2**43 + 5, 2**52, 2**62], dtype=np.uint64)
+    ginv = pow(G, -1, 2**63)
+    pre = np.array([((int(x) - CC) * ginv) % 2**63 for x in special], dtype=np.uint64)
+    pre = np.concatenate([pre, oracle.seed_hash(M, 1, 0, 101)])
+    v = torch.from_numpy(pre.view(np.int64).copy()).cuda()
+    dg = torch.empty(pre.size, dtype=torch.int64, device="cuda")
+    mc.mc_lcg_draw(ctx, mc.make_lcg(), None, 0, v, pre.size, draws, None, dg)
+    o_st, _, o_dg = oracle.lcg_draw(M, G, CC, pre, draws, want_u=False)
+    assert np.array_equal(u64(v), o_st)
+    assert np.array_equal(u64(dg), o_dg)
