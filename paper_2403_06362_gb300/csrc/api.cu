@@ -4,6 +4,7 @@
 // and conversion of int64 fixed-point tallies to flux.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -172,6 +173,8 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   ctx->problems.release();
   ctx->bank.release();
   if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
+  if (ctx->h_done) cudaFreeHost(ctx->h_done);
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }
 
@@ -236,6 +239,17 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
   L.block = cfg->block ? (int)cfg->block : 256;
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
+  if (cfg->schedule == MC_SCHED_EVENT) {
+    // Bank of up to 2^20 particles (about 100 MiB); allocated on first use.
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(L.total, 1u << 20);
+    st = ctx->bank.reserve(mci::slab_bank_bytes(cap));
+    if (st != MC_OK) return st;
+    if (!ctx->h_done) MC_TRY_CUDA(cudaMallocHost(&ctx->h_done, sizeof(unsigned int)));
+    if (cfg->use_graph && !ctx->capture_stream)
+      MC_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    return mci::slab_event_run(L, ctx->bank.ptr, cap, ctx->h_done, cfg->use_graph ? ctx->capture_stream : nullptr,
+                               s);
+  }
   return mci::slab_history_launch(L, s);
 }
 

@@ -50,7 +50,11 @@ struct mc_ctx {
   void* h_problems = nullptr;
   size_t h_problems_bytes = 0;
   cudaEvent_t staged = nullptr;  // recorded after the last upload from h_problems
-  // Event-based schedule: particle banks.
+  // Event-based schedule: particle bank and a pinned completion flag.
   mci::DeviceBuf bank;
+  unsigned int* h_done = nullptr;
+  // Private stream used only to capture graphs (the caller's stream may be
+  // the legacy default stream, which cannot be captured).
+  cudaStream_t capture_stream = nullptr;
   mci::GraphCache* graphs = nullptr;
 };

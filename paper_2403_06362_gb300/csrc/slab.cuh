@@ -158,8 +158,8 @@ struct SlabParticle {
   float xf, muf, wf;
 };
 
-// Outcome of one flight (+ collision).
-enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3 };
+// Outcome of a flight or a collision.
+enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3, kCollide = 4 };
 
 // Source of a history (isotropic uniform in [0, L], or a beam at x = 0).
 template <int M, bool F32>
@@ -182,12 +182,11 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
   }
 }
 
-// One flight and, if the particle stays in the slab, one collision.
-// Counters: *coll and *scat are incremented here; the caller counts the
-// flight and the outcome.
+// One flight: sample the distance, tally the track, and either leak
+// (kLeakLo / kLeakHi) or stop at the collision site (kCollide).
 template <int M, bool F32>
-__device__ __forceinline__ int slab_event(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q,
-                                          const Sink& s, uint32_t& coll, uint32_t& scat) {
+__device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q,
+                                           const Sink& s) {
   const double u = r.next(l);
   if constexpr (!F32) {
     const double d = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
@@ -224,9 +223,14 @@ __device__ __forceinline__ int slab_event(const SlabDev& p, Rng<M>& r, const mcd
     else seg32(p, xn, q.xf, q.wf, s);
     q.xf = xn;
   }
-  ++coll;
+  return kCollide;
+}
+
+// One collision at the current site: absorption (kAbsorbed) or isotropic
+// scattering into a new direction (kContinue).
+template <int M, bool F32>
+__device__ __forceinline__ int slab_collide(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
   if (r.next(l) < p.p_abs) return kAbsorbed;
-  ++scat;
   const double u2 = r.next(l);
   if constexpr (!F32) {
     q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
@@ -236,6 +240,19 @@ __device__ __forceinline__ int slab_event(const SlabDev& p, Rng<M>& r, const mcd
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
   }
   return kContinue;
+}
+
+// One flight and, if the particle stays in the slab, one collision (the
+// history-based step).  Counts collisions and scatters into *coll, *scat.
+template <int M, bool F32>
+__device__ __forceinline__ int slab_event(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q,
+                                          const Sink& s, uint32_t& coll, uint32_t& scat) {
+  const int f = slab_flight<M, F32>(p, r, l, q, s);
+  if (f != kCollide) return f;
+  ++coll;
+  const int c = slab_collide<M, F32>(p, r, l, q);
+  if (c == kContinue) ++scat;
+  return c;
 }
 
 }  // namespace mcs

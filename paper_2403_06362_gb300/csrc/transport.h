@@ -29,4 +29,12 @@ void slab_fill_host(const mc_problem* src, uint32_t n, void* dst);
 int slab_prep(void* d_probs, uint32_t n, cudaStream_t s);
 int slab_history_launch(const SlabLaunch& L, cudaStream_t s);
 
+// Event-based schedule (slab_event.cu): bank of `cap` particles in d_bank
+// (slab_bank_bytes(cap) bytes); h_done is pinned host memory.  Synchronises
+// `s` between batches of iterations.  capture_stream non-null: each batch is
+// captured once on it into a graph, which is then launched on `s`.
+size_t slab_bank_bytes(uint32_t cap);
+int slab_event_run(const SlabLaunch& L, void* d_bank, uint32_t cap, unsigned int* h_done,
+                   cudaStream_t capture_stream, cudaStream_t s);
+
 }  // namespace mci

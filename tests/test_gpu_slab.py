@@ -182,3 +182,46 @@ def test_fp32_guarded_error_stated(env, oracle):
     assert rel.max() < 2e-2, rel.max()
     c32 = counts_of(t32, 1)[0]
     assert int(c32[0]) == int(c32[3]) + int(c32[5]) + int(c32[6])
+
+
+def _same_bits(a, b, n):
+    assert np.array_equal(a.bins.cpu().numpy(), b.bins.cpu().numpy())
+    assert np.array_equal(counts_of(a, n), counts_of(b, n))
+    if a.hist_state is not None and b.hist_state is not None:
+        assert np.array_equal(a.hist_state.cpu().numpy(), b.hist_state.cpu().numpy())
+        assert np.array_equal(a.hist_draws.cpu().numpy(), b.hist_draws.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("use_graph", [0, 1])
+@pytest.mark.parametrize("which", ["small_hash", "small_stride", "batched", "long"])
+def test_event_schedule_bit_identical_to_history(env, oracle, precision, use_graph, which):
+    if which == "small_hash":
+        probs = W.slab_small(W.SEED_HASH)
+    elif which == "small_stride":
+        probs = W.slab_small(W.SEED_STRIDE)
+    elif which == "batched":
+        probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=30, max_histories=4000)
+    else:
+        probs = W.slab_long(W.SEED_STRIDE, n_histories=5000)
+    hist, _ = gpu_run(env, probs, precision=precision)
+    ev, _ = gpu_run(env, probs, precision=precision, schedule=1, use_graph=use_graph)
+    _same_bits(hist, ev, len(probs))
+    if precision == 0 and which == "small_hash":
+        o = oracle_run(oracle, probs)
+        assert np.array_equal(ev.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+        assert_tally_close(ev.bins.cpu().numpy(), o["tally"])
+
+
+def test_event_schedule_event_cap_and_ranges(env):
+    mc, ctx, torch = env
+    p = [W.slab_problem(200.0, 1.0, 0.9999, 300, 10, 1, W.SEED_HASH)]
+    a, _ = gpu_run(env, p, event_cap=40)
+    b, _ = gpu_run(env, p, event_cap=40, schedule=1)
+    _same_bits(a, b, 1)
+    assert counts_of(b, 1)[0, 12] > 0
+    # a sub-range in event mode equals the same sub-range in history mode
+    probs = W.slab_small(W.SEED_HASH)
+    a, _ = gpu_run(env, probs, range_begin=123, range_end=4567)
+    b, _ = gpu_run(env, probs, range_begin=123, range_end=4567, schedule=1)
+    _same_bits(a, b, 1)
