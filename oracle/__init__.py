@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mc_oracle_box.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 NCOUNT = 16
@@ -33,13 +34,12 @@ SRC_ISOTROPIC, SRC_BEAM = 0, 1
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2 -ffp-contract=off, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
-        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "mc_oracle.h"))
-    ):
+    newest = max(os.path.getmtime(f) for f in _SRCS + [os.path.join(_HERE, "mc_oracle.h")])
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
             ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-fPIC",
-             "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
+             "-shared", "-Wall", "-o", tmp, *_SRCS, "-lm"]
         )
         os.replace(tmp, _LIB)
     return _LIB
@@ -47,6 +47,22 @@ def build(force: bool = False) -> str:
 
 class Lcg(C.Structure):
     _fields_ = [("m", C.c_uint32), ("pad", C.c_uint32), ("g", C.c_uint64), ("c", C.c_uint64)]
+
+
+BOX_MAX_GROUPS = 8
+
+
+class BoxProblem(C.Structure):
+    _fields_ = [
+        ("side", C.c_double), ("inner_lo", C.c_double), ("inner_hi", C.c_double),
+        ("sigma_t", C.c_double * 2), ("c", C.c_double * 2),
+        ("ww_low", C.c_double * 2), ("ww_high", C.c_double * 2), ("ww_survive", C.c_double * 2),
+        ("cdf", ((C.c_double * BOX_MAX_GROUPS) * BOX_MAX_GROUPS) * 2),
+        ("n_histories", C.c_uint64), ("seed", C.c_uint64), ("stride_q", C.c_uint64),
+        ("id_offset", C.c_uint64), ("key", C.c_uint64), ("tally_offset", C.c_uint64),
+        ("n_groups", C.c_uint32), ("mesh", C.c_uint32), ("max_split", C.c_uint32),
+        ("n_batches", C.c_uint32), ("seeding", C.c_uint32), ("source", C.c_uint32),
+    ]
 
 
 class SlabProblem(C.Structure):
@@ -90,6 +106,14 @@ def lib():
             L.or_slab_run.restype = C.c_int
             L.or_slab_run.argtypes = [C.POINTER(Lcg), C.POINTER(SlabProblem), u64, u64, u64,
                                       P, P, P, P, P]
+            BP = C.POINTER(BoxProblem)
+            L.or_box_seed.restype = u64; L.or_box_seed.argtypes = [C.POINTER(Lcg), BP, u64]
+            L.or_box_run.restype = C.c_int
+            L.or_box_run.argtypes = [C.POINTER(Lcg), BP, u64, u64, u64, P, P, P, P, P]
+            L.or_box_iso_dir.restype = u64; L.or_box_iso_dir.argtypes = [C.POINTER(Lcg), u64, P]
+            L.or_box_trace.restype = None; L.or_box_trace.argtypes = [BP, P, P, dbl, dbl, P, P]
+            L.or_box_surface_dist.restype = dbl
+            L.or_box_surface_dist.argtypes = [BP, P, P, u32, C.POINTER(C.c_int)]
             L.or_norm_cdf.restype = dbl; L.or_norm_cdf.argtypes = [dbl]
             L.or_norm_ppf.restype = dbl; L.or_norm_ppf.argtypes = [dbl]
             L.or_shapiro_wilk.restype = C.c_int
@@ -253,3 +277,53 @@ def batch_stats(x):
 def slab_seed(lcg: Lcg, prob: SlabProblem, local_id: int) -> int:
     """Seed of local history `local_id` (Eq. 3 / Eq. 4 / stride X_{Qk})."""
     return int(lib().or_slab_seed(C.byref(lcg), C.byref(prob), local_id))
+
+
+# --- two-region box (mc_oracle_box.c) --------------------------------------------
+
+def box_run(lcg: Lcg, prob: BoxProblem, id_begin=0, id_end=None, event_cap=2**62, tally=None,
+            tally_fp=None, counts=None, per_history=False):
+    if id_end is None:
+        id_end = int(prob.n_histories)
+    nvox = int(prob.mesh) ** 3
+    size = int(prob.tally_offset) + int(prob.n_batches) * nvox
+    if tally is None:
+        tally = np.zeros(size, dtype=np.int64)
+    if tally_fp is None:
+        tally_fp = np.zeros(size, dtype=np.float64)
+    if counts is None:
+        counts = np.zeros(NCOUNT, dtype=np.uint64)
+    n = id_end - id_begin
+    hs = np.zeros(n, dtype=np.uint64) if per_history else None
+    hd = np.zeros(n, dtype=np.uint64) if per_history else None
+    st = lib().or_box_run(C.byref(lcg), C.byref(prob), id_begin, id_end, event_cap, _ptr(tally),
+                          _ptr(tally_fp), _ptr(counts), _ptr(hs), _ptr(hd))
+    return dict(status=st, tally=tally, tally_fp=tally_fp, counts=counts, hist_state=hs, hist_draws=hd)
+
+
+def box_seed(lcg: Lcg, prob: BoxProblem, local_id: int) -> int:
+    return int(lib().or_box_seed(C.byref(lcg), C.byref(prob), local_id))
+
+
+def box_iso_dir(lcg: Lcg, x: int):
+    u = np.zeros(3)
+    draws = int(lib().or_box_iso_dir(C.byref(lcg), x, _ptr(u)))
+    return u, draws
+
+
+def box_trace(prob: BoxProblem, p, u, L, w=1.0):
+    nvox = int(prob.mesh) ** 3
+    t64 = np.zeros(nvox, dtype=np.int64)
+    tf = np.zeros(nvox)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib().or_box_trace(C.byref(prob), _ptr(p), _ptr(u), L, w, _ptr(t64), _ptr(tf))
+    return t64, tf
+
+
+def box_surface_dist(prob: BoxProblem, p, u, region):
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    k = C.c_int(0)
+    d = float(lib().or_box_surface_dist(C.byref(prob), _ptr(p), _ptr(u), region, C.byref(k)))
+    return d, int(k.value)

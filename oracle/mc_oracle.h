@@ -76,6 +76,27 @@ int or_slab_run(const or_lcg* l, const or_slab_problem* p, uint64_t id_begin, ui
                 uint64_t event_cap, int64_t* tally, double* tally_fp, uint64_t* counts,
                 uint64_t* hist_state, uint64_t* hist_draws);
 
+/* Two-region multigroup box with weight windows (mc_oracle_box.c). */
+#define OR_BOX_MAX_GROUPS 8
+typedef struct {
+    double side, inner_lo, inner_hi;
+    double sigma_t[2], c[2];                 /* region 0 = outer, 1 = inner */
+    double ww_low[2], ww_high[2], ww_survive[2];
+    double cdf[2][OR_BOX_MAX_GROUPS][OR_BOX_MAX_GROUPS]; /* [region][g][g'] */
+    uint64_t n_histories, seed, stride_q, id_offset, key, tally_offset;
+    uint32_t n_groups, mesh, max_split, n_batches;
+    uint32_t seeding, source;
+} or_box_problem;
+
+uint64_t or_box_seed(const or_lcg* l, const or_box_problem* b, uint64_t id);
+int or_box_run(const or_lcg* l, const or_box_problem* b, uint64_t id_begin, uint64_t id_end, uint64_t event_cap,
+               int64_t* tally, double* tally_fp, uint64_t* counts, uint64_t* hist_state, uint64_t* hist_draws);
+uint64_t or_box_iso_dir(const or_lcg* l, uint64_t x, double* u_out);
+void or_box_trace(const or_box_problem* b, const double* p, const double* u, double L, double w, int64_t* t64,
+                  double* tfp);
+double or_box_surface_dist(const or_box_problem* b, const double* p, const double* u, uint32_t region,
+                           int* kind_out);
+
 double or_norm_cdf(double z);
 double or_norm_ppf(double p);
 int or_shapiro_wilk(const double* x, int n, double* w, double* p);

@@ -94,3 +94,71 @@ def to_oracle_problem(p, oracle):
                               seed=p["seed"], stride_q=p["stride_q"], id_offset=p["id_offset"],
                               key=p["key"], tally_offset=p["tally_offset"], n_bins=p["n_bins"],
                               n_batches=p["n_batches"], source=p["source"], seeding=p["seeding"])
+
+
+# --- two-region multigroup box ------------------------------------------------
+#   box_large  100 cm cube, inner cube [30, 70]^3 (Sigma_t 2.0/cm, c 0.3) in an
+#              outer region (Sigma_t 0.5/cm, c 0.95); 4 groups with a
+#              downscatter matrix drawn from numpy seed 3; implicit capture;
+#              weight windows (w_low, w_high, w_survive): outer (0.25, 2.0, 0.5),
+#              inner (0.02, 0.1, 0.05); splits of at most 8; isotropic source
+#              uniform in the box, group 0; 64^3 group-summed track-length mesh;
+#              10^8 histories, one batch
+
+BOX_MAX_GROUPS = 8
+
+
+def downscatter_cdf(n_groups=4, seed=3):
+    """CDF rows [region][g][g'] of a lower-triangular downscatter matrix
+    (g -> g' >= g) with random positive entries; the last group scatters to
+    itself only.  Entries below the diagonal are 0; every row ends at 1.0."""
+    rng = np.random.default_rng(seed)
+    cdf = np.zeros((2, BOX_MAX_GROUPS, BOX_MAX_GROUPS))
+    for r in range(2):
+        for g in range(n_groups):
+            w = rng.random(n_groups - g) + 0.05
+            c = np.cumsum(w / w.sum())
+            c[-1] = 1.0
+            cdf[r, g, g:n_groups] = c
+            cdf[r, g, n_groups:] = 1.0
+    return cdf
+
+
+def box_problem(n_histories=10**8, seeding=SEED_HASH, side=100.0, inner=(30.0, 70.0),
+                sigma_t=(0.5, 2.0), c=(0.95, 0.3), ww_low=(0.25, 0.02), ww_high=(2.0, 0.1),
+                ww_survive=(0.5, 0.05), n_groups=4, mesh=64, max_split=8, n_batches=1,
+                tally_offset=0, seed=None, cdf_seed=3):
+    if seed is None:
+        seed = STRIDE_X0 if seeding == SEED_STRIDE else HASH_SEED
+    return dict(side=float(side), inner_lo=float(inner[0]), inner_hi=float(inner[1]),
+                sigma_t=tuple(float(v) for v in sigma_t), c=tuple(float(v) for v in c),
+                ww_low=tuple(float(v) for v in ww_low), ww_high=tuple(float(v) for v in ww_high),
+                ww_survive=tuple(float(v) for v in ww_survive),
+                cdf=downscatter_cdf(n_groups, cdf_seed), n_groups=int(n_groups), mesh=int(mesh),
+                max_split=int(max_split), n_batches=int(n_batches), n_histories=int(n_histories),
+                seeding=int(seeding), seed=int(seed), stride_q=STRIDE_Q, id_offset=0, key=0,
+                tally_offset=int(tally_offset), source=SRC_ISOTROPIC)
+
+
+def box_large(seeding=SEED_HASH, n_histories=10**8):
+    return box_problem(n_histories=n_histories, seeding=seeding)
+
+
+def box_tally_slots(b):
+    return b["tally_offset"] + b["n_batches"] * b["mesh"] ** 3
+
+
+def to_oracle_box(b, oracle):
+    o = oracle.BoxProblem()
+    o.side, o.inner_lo, o.inner_hi = b["side"], b["inner_lo"], b["inner_hi"]
+    for r in range(2):
+        o.sigma_t[r], o.c[r] = b["sigma_t"][r], b["c"][r]
+        o.ww_low[r], o.ww_high[r], o.ww_survive[r] = b["ww_low"][r], b["ww_high"][r], b["ww_survive"][r]
+        for g in range(BOX_MAX_GROUPS):
+            for h in range(BOX_MAX_GROUPS):
+                o.cdf[r][g][h] = b["cdf"][r, g, h]
+    o.n_histories, o.seed, o.stride_q = b["n_histories"], b["seed"], b["stride_q"]
+    o.id_offset, o.key, o.tally_offset = b["id_offset"], b["key"], b["tally_offset"]
+    o.n_groups, o.mesh, o.max_split, o.n_batches = b["n_groups"], b["mesh"], b["max_split"], b["n_batches"]
+    o.seeding, o.source = b["seeding"], b["source"]
+    return o
