@@ -80,7 +80,8 @@ constexpr size_t kTicketOff = 0;     // unsigned long long ticket
 constexpr size_t kScratchBytes = 256;
 
 int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStream_t s) {
-  const size_t bytes = (size_t)n * mci::slab_dev_size();
+  const bool box = problems[0].geometry == MC_GEOM_BOX;
+  const size_t bytes = (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
   cudaEvent_t* ev = &ctx->staged;
   if (*ev) MC_TRY_CUDA(cudaEventSynchronize(*ev));
   if (bytes > ctx->h_problems_bytes) {
@@ -92,20 +93,59 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
   }
   int st = ctx->problems.reserve(bytes);
   if (st != MC_OK) return st;
-  mci::slab_fill_host(problems, n, ctx->h_problems);
+  if (box) mci::box_fill_host(problems, n, ctx->h_problems);
+  else mci::slab_fill_host(problems, n, ctx->h_problems);
   MC_TRY_CUDA(cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, s));
   if (!*ev) MC_TRY_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   MC_TRY_CUDA(cudaEventRecord(*ev, s));
-  return mci::slab_prep(ctx->problems.ptr, n, s);
+  return box ? mci::box_prep(ctx->problems.ptr, n, s) : mci::slab_prep(ctx->problems.ptr, n, s);
+}
+
+int check_box(const mc_problem& q, uint32_t i) {
+  const mc_box_spec* b = q.box;
+  if (!b) {
+    mci::set_error("problem %u: box geometry without a box spec", i);
+    return MC_ERR_ARG;
+  }
+  bool ok = b->side > 0.0 && std::isfinite(b->side) && b->inner_lo >= 0.0 && b->inner_lo < b->inner_hi &&
+            b->inner_hi <= b->side && b->n_groups >= 1 && b->n_groups <= MC_BOX_MAX_GROUPS && b->mesh >= 1 &&
+            b->mesh <= 1024 && b->max_split >= 1 && b->reserved == 0 &&
+            (uint64_t)q.n_bins == (uint64_t)b->mesh * b->mesh * b->mesh;
+  for (int r = 0; r < 2 && ok; ++r) {
+    ok = b->sigma_t[r] > 0.0 && std::isfinite(b->sigma_t[r]) && b->c[r] >= 0.0 && b->c[r] <= 1.0 &&
+         b->ww_low[r] >= 0.0 && b->ww_survive[r] > 0.0 && b->ww_high[r] > 0.0;
+    for (uint32_t g = 0; g < b->n_groups && ok; ++g) ok = b->scatter_cdf[r][g][b->n_groups - 1] == 1.0;
+  }
+  if (!ok) {
+    mci::set_error("problem %u: invalid box spec (extents, groups, mesh, windows, or a CDF row not ending at 1)",
+                   i);
+    return MC_ERR_ARG;
+  }
+  return MC_OK;
 }
 
 int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t* total) {
   uint64_t acc = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const mc_problem& q = p[i];
-    if (q.geometry != MC_GEOM_SLAB) {
-      mci::set_error("problem %u: only slab geometry is supported by this entry point", i);
+    if (q.geometry != p[0].geometry || q.geometry > MC_GEOM_BOX) {
+      mci::set_error("problem %u: all problems of one call must share one geometry (slab or box)", i);
       return MC_ERR_ARG;
+    }
+    if (q.geometry == MC_GEOM_BOX) {
+      int st = check_box(q, i);
+      if (st != MC_OK) return st;
+      if (q.n_batches == 0 || q.source != MC_SRC_ISOTROPIC || q.seeding > MC_SEED_HASH_HIER || q.reserved != 0) {
+        mci::set_error("problem %u: bad n_batches/source/seeding for a box", i);
+        return MC_ERR_ARG;
+      }
+      const uint64_t slots = (uint64_t)q.n_bins * q.n_batches;
+      if (q.tally_offset > t->n_slots || slots > t->n_slots - q.tally_offset) {
+        mci::set_error("problem %u: mesh slots outside the tally", i);
+        return MC_ERR_ARG;
+      }
+      acc += q.n_histories;
+      continue;
     }
     if (!(q.L > 0.0) || !(q.sigma_t > 0.0) || !(q.c >= 0.0 && q.c <= 1.0) || !std::isfinite(q.L) ||
         !std::isfinite(q.sigma_t)) {
@@ -128,6 +168,53 @@ int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t*
   }
   *total = acc;
   return MC_OK;
+}
+
+constexpr uint64_t kChildCap = 1ull << 22;      // child records per bank
+constexpr uint64_t kPrimaryChunk = 1ull << 21;  // source histories per generation-0 launch
+
+int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_config* cfg, const mc_tally* tally,
+            uint64_t rb, uint64_t re, unsigned long long* ticket, cudaStream_t s) {
+  const size_t rec = mci::box_child_rec_size();
+  int st = ctx->children.reserve(2 * kChildCap * rec);
+  if (st != MC_OK) return st;
+  if (!ctx->h_count) MC_TRY_CUDA(cudaMallocHost(&ctx->h_count, sizeof(unsigned long long)));
+  mci::BoxLaunch L{};
+  L.d_probs = ctx->problems.ptr;
+  L.n_problems = n_problems;
+  L.chunk = cfg->chunk ? cfg->chunk : 64u;
+  L.range_begin = rb;
+  L.total = re - rb;
+  L.primary_chunk = kPrimaryChunk;
+  L.d_ticket = ticket;
+  L.d_child[0] = ctx->children.ptr;
+  L.d_child[1] = static_cast<char*>(ctx->children.ptr) + kChildCap * rec;
+  L.d_child_count = ticket + 1;  // scratch words 1 and 2
+  L.h_count = ctx->h_count;
+  L.child_cap = kChildCap;
+  L.tally = tally;
+  L.lcg = *lcg;
+  // Box particles end by leaking or by roulette within a few hundred flights;
+  // the default cap of 2^22 flights per particle only bounds pathologies.
+  L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 22);
+  L.f32 = cfg->precision == MC_FP32_GUARDED;
+  L.block = cfg->block ? (int)cfg->block : 256;
+  L.blocks_per_sm = (int)cfg->blocks_per_sm;
+  L.num_sms = ctx->num_sms;
+  if (cfg->schedule == MC_SCHED_EVENT) {
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.total, 1), 1u << 20);
+    st = ctx->bank.reserve(mci::box_bank_bytes(cap));
+    if (st != MC_OK) return st;
+    if (!ctx->h_done) MC_TRY_CUDA(cudaMallocHost(&ctx->h_done, sizeof(unsigned int)));
+    if (cfg->use_graph && !ctx->capture_stream)
+      MC_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    L.d_bank = ctx->bank.ptr;
+    L.bank_cap = cap;
+    L.h_done = ctx->h_done;
+    L.capture_stream = cfg->use_graph ? ctx->capture_stream : nullptr;
+    return mci::box_event_run(L, s);
+  }
+  return mci::box_history_run(L, s);
 }
 
 }  // namespace
@@ -174,6 +261,8 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   ctx->bank.release();
   if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
   if (ctx->h_done) cudaFreeHost(ctx->h_done);
+  if (ctx->h_count) cudaFreeHost(ctx->h_count);
+  ctx->children.release();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }
@@ -215,6 +304,8 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
   auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
   MC_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
   if (re == rb) return MC_OK;
+
+  if (problems[0].geometry == MC_GEOM_BOX) return run_box(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, s);
 
   mci::SlabLaunch L{};
   L.d_probs = ctx->problems.ptr;
@@ -279,8 +370,12 @@ MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t probl
   if (h_raw) std::memcpy(h_raw, raw.data(), slots * sizeof(int64_t));
   if (h_counts) std::memcpy(h_counts, cnt.data(), MC_NCOUNT * sizeof(uint64_t));
 
-  // Cell volume per bin: slab width L/n_bins.
-  const double vol = p.L / (double)nb;
+  // Cell volume per bin: slab width L/n_bins, or the cube of the mesh pitch.
+  double vol = p.L / (double)nb;
+  if (p.geometry == MC_GEOM_BOX && p.box) {
+    const double h = p.box->side / (double)p.box->mesh;
+    vol = h * h * h;
+  }
   const double scale = std::ldexp(1.0, -32);
   const uint64_t N = p.n_histories;
   bool overflow = false;

@@ -1,0 +1,330 @@
+// box.cuh -- device physics of the two-region multigroup box, shared by the
+// history-based (box.cu) and event-based (box_event.cu) schedules.
+//
+// Geometry: box [0,S]^3 with an inner cube [lo,hi]^3 (region 1) inside the
+// outer region 0, vacuum outside.  Surface tracking: each flight samples
+// d = -ln(1-u) / Sigma_t[region] and stops at the region surface if that is
+// nearer.  Collisions: implicit capture, downscatter by CDF row, isotropic
+// direction by Marsaglia's rejection method, then the region's weight window
+// (roulette or split).  Children of a split are seeded on demand with
+// S_c = hash(k, S_p) (Section 4, Eq. 5) from the parent's current state.
+// Track lengths go to a group-summed mesh as int64 fixed point (2^32).
+//
+// T = double: every operation rounds once (this code is compiled with
+// --fmad=false), matching the fp64 transport definition step for step.
+// T = float: geometry and distances in fp32; a flight whose fp32 collision
+// distance lies within a relative 2^-16 of the surface distance is decided
+// again in fp64; uniforms, hashes and the fixed-point scaling stay exact.
+#pragma once
+#include <cstdint>
+
+#include "../../include/mc.h"
+#include "mc_device.cuh"
+#include "slab.cuh"
+
+namespace mcb {
+
+constexpr int kMaxG = MC_BOX_MAX_GROUPS;
+
+struct BoxDev {
+  double side, lo, hi;
+  double st[2], c[2], wl[2], wh[2], ws[2];
+  double cdf[2][kMaxG][kMaxG];
+  uint64_t n_hist, seed, stride_q, id_offset, key, tally_offset;
+  uint32_t ng, mesh, max_split, n_batches, seeding, source;
+  // derived on the device (box_prep_kernel)
+  double inv_st[2], h, inv_h;
+  float side_f, lo_f, hi_f, h_f, inv_h_f;
+  float inv_st_f[2], c_f[2], wl_f[2], wh_f[2], ws_f[2];
+  uint64_t seed_hash, hist_begin;
+};
+
+// A particle of the box (position, direction and its componentwise inverse,
+// weight, group, region).
+template <typename T>
+struct Part {
+  T p[3], u[3], inv[3];
+  T w;
+  uint32_t g, region;
+};
+
+// Record of a split child waiting in a device bank (fp64 fields; fp32
+// particles store their values exactly).
+struct ChildRec {
+  double p[3], u[3], w;
+  uint64_t rng;
+  uint64_t tbase;  // tally slot row of the family (problem offset + batch row)
+  uint32_t g, region, prob, pad;
+};
+
+enum BoxOutcome : int { kBoxCollide = 0, kBoxCross = 1, kBoxLeak = 2, kBoxContinue = 3, kBoxKilled = 4 };
+
+template <typename T> __device__ __forceinline__ T from_u(double u);
+template <> __device__ __forceinline__ double from_u<double>(double u) { return u; }
+template <> __device__ __forceinline__ float from_u<float>(double u) { return (float)u; }
+
+template <typename T> __device__ __forceinline__ T sel(const double& d, const float& f);
+template <> __device__ __forceinline__ double sel<double>(const double& d, const float&) { return d; }
+template <> __device__ __forceinline__ float sel<float>(const double&, const float& f) { return f; }
+
+template <typename T>
+__device__ __forceinline__ void set_inv(Part<T>& q) {
+  for (int a = 0; a < 3; ++a) q.inv[a] = q.u[a] != T(0) ? T(1) / q.u[a] : T(0);
+}
+
+// Marsaglia (1972): v1, v2 uniform on [-1,1)^2 until v1^2 + v2^2 < 1.
+template <int M, typename T>
+__device__ __forceinline__ void iso_dir(mcs::Rng<M>& r, const mcd::Lcg& l, T u[3]) {
+  T v1, v2, s;
+  do {
+    v1 = T(2) * from_u<T>(r.next(l)) - T(1);
+    v2 = T(2) * from_u<T>(r.next(l)) - T(1);
+    s = v1 * v1 + v2 * v2;
+  } while (s >= T(1));
+  const T t = sqrt(T(1) - s);
+  u[0] = T(2) * v1 * t;
+  u[1] = T(2) * v2 * t;
+  u[2] = T(1) - T(2) * s;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t region_of(const BoxDev& b, const T p[3], const T u[3]) {
+  const T lo = sel<T>(b.lo, b.lo_f), hi = sel<T>(b.hi, b.hi_f);
+  for (int a = 0; a < 3; ++a) {
+    const bool above = p[a] > lo || (p[a] == lo && u[a] > T(0));
+    const bool below = p[a] < hi || (p[a] == hi && u[a] < T(0));
+    if (!above || !below) return 0u;
+  }
+  return 1u;
+}
+
+template <typename T>
+__device__ __forceinline__ T exit_dist(const Part<T>& q, T lo, T hi) {
+  T t = T(INFINITY);
+  for (int a = 0; a < 3; ++a) {
+    T ta;
+    if (q.u[a] > T(0)) ta = (hi - q.p[a]) * q.inv[a];
+    else if (q.u[a] < T(0)) ta = (lo - q.p[a]) * q.inv[a];
+    else continue;
+    if (ta < t) t = ta;
+  }
+  return t < T(0) ? T(0) : t;
+}
+
+template <typename T>
+__device__ __forceinline__ T entry_dist(const Part<T>& q, T lo, T hi) {
+  T tn = T(-INFINITY), tf = T(INFINITY);
+  for (int a = 0; a < 3; ++a) {
+    if (q.u[a] != T(0)) {
+      const T t1 = (lo - q.p[a]) * q.inv[a], t2 = (hi - q.p[a]) * q.inv[a];
+      const T tmin = t1 < t2 ? t1 : t2, tmax = t1 < t2 ? t2 : t1;
+      if (tmin > tn) tn = tmin;
+      if (tmax < tf) tf = tmax;
+    } else if (q.p[a] <= lo || q.p[a] >= hi) {
+      return T(INFINITY);
+    }
+  }
+  if (tn >= T(0) && tn < tf) return tn;
+  return T(INFINITY);
+}
+
+// Distance to the region surface and its kind (1: into the other region,
+// 2: out of the box).
+template <typename T>
+__device__ __forceinline__ T surface(const BoxDev& b, const Part<T>& q, int& kind) {
+  const T lo = sel<T>(b.lo, b.lo_f), hi = sel<T>(b.hi, b.hi_f), side = sel<T>(b.side, b.side_f);
+  if (q.region == 1u) {
+    kind = 1;
+    return exit_dist(q, lo, hi);
+  }
+  const T de = entry_dist(q, lo, hi);
+  const T dx = exit_dist(q, T(0), side);
+  kind = de < dx ? 1 : 2;
+  return de < dx ? de : dx;
+}
+
+__device__ __forceinline__ long long fix_of(double wl) { return __double2ll_rn(wl * mcs::kFix); }
+__device__ __forceinline__ long long fix_of(float wl) { return mcs::fix32_from_float(wl); }
+
+template <typename T>
+__device__ __forceinline__ T plane(const BoxDev& b, int j) {
+  return j >= (int)b.mesh ? sel<T>(b.side, b.side_f) : (T)j * sel<T>(b.h, b.h_f);
+}
+
+// Track-length tally of p + t u, 0 <= t <= L, by a voxel walk: the next
+// crossing on each axis is computed from the segment start directly,
+// t = (plane - p) / u, so every piece has the length the clipping definition
+// gives it.  base: this history's [mesh^3] slot row.
+template <typename T>
+__device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long* base) {
+  const int nm = (int)b.mesh;
+  const T h = sel<T>(b.h, b.h_f), inv_h = sel<T>(b.inv_h, b.inv_h_f);
+  int idx[3];
+  T tn[3];
+  for (int a = 0; a < 3; ++a) {
+    int i = (int)floor(q.p[a] * inv_h);
+    i = i < 0 ? 0 : (i >= nm ? nm - 1 : i);
+    while (i > 0 && q.p[a] < plane<T>(b, i)) --i;
+    while (i + 1 < nm && q.p[a] >= plane<T>(b, i + 1)) ++i;
+    if (q.u[a] < T(0) && i > 0 && q.p[a] == plane<T>(b, i)) --i;
+    idx[a] = i;
+    if (q.u[a] > T(0)) tn[a] = (plane<T>(b, i + 1) - q.p[a]) * q.inv[a];
+    else if (q.u[a] < T(0)) tn[a] = (plane<T>(b, i) - q.p[a]) * q.inv[a];
+    else tn[a] = T(INFINITY);
+  }
+  (void)h;
+  T t = T(0);
+  const T w = q.w;
+  for (int guard = 0; guard < 3 * nm + 8; ++guard) {
+    int a = 0;
+    if (tn[1] < tn[a]) a = 1;
+    if (tn[2] < tn[a]) a = 2;
+    const T tend = tn[a] < L ? tn[a] : L;
+    if (tend > t) {
+      const long long v = fix_of(w * (tend - t));
+      if (v != 0) {
+        const uint64_t slot = ((uint64_t)idx[2] * nm + idx[1]) * nm + idx[0];
+        atomicAdd(base + slot, (unsigned long long)v);
+      }
+      t = tend;
+    }
+    if (!(tn[a] < L)) break;
+    // step across the plane on axis a
+    if (q.u[a] > T(0)) {
+      idx[a] += 1;
+      if (idx[a] >= nm) break;
+      tn[a] = (plane<T>(b, idx[a] + 1) - q.p[a]) * q.inv[a];
+    } else {
+      idx[a] -= 1;
+      if (idx[a] < 0) break;
+      tn[a] = (plane<T>(b, idx[a]) - q.p[a]) * q.inv[a];
+    }
+  }
+}
+
+template <int M, typename T>
+__device__ __forceinline__ void box_source(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q) {
+  const T side = sel<T>(b.side, b.side_f);
+  for (int a = 0; a < 3; ++a) q.p[a] = side * from_u<T>(r.next(l));
+  iso_dir<M, T>(r, l, q.u);
+  set_inv(q);
+  q.w = T(1);
+  q.g = 0u;
+  q.region = region_of<T>(b, q.p, q.u);
+}
+
+// One flight: collide (position moved to the site), cross into the other
+// region (moved to the surface), or leak out of the box.
+template <int M, typename T>
+__device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q,
+                                          unsigned long long* base) {
+  const double u = r.next(l);
+  int kind = 0;
+  T ds = surface<T>(b, q, kind);
+  bool collide;
+  T d;
+  if constexpr (sizeof(T) == 8) {
+    d = -log(1.0 - u) * b.inv_st[q.region];
+    collide = d < ds;
+  } else {
+    d = -log1pf(-(float)u) * b.inv_st_f[q.region];
+    collide = d < ds;
+    if (fabsf(d - ds) <= 0x1p-16f * fmaxf(d, ds)) {  // near the surface: decide in fp64
+      Part<double> q64;
+      for (int a = 0; a < 3; ++a) {
+        q64.p[a] = q.p[a];
+        q64.u[a] = q.u[a];
+        q64.inv[a] = q.inv[a] != 0.0f ? 1.0 / (double)q.u[a] : 0.0;
+      }
+      q64.region = q.region;
+      int k64 = 0;
+      const double ds64 = surface<double>(b, q64, k64);
+      const double d64 = -log(1.0 - u) * b.inv_st[q.region];
+      collide = d64 < ds64;
+      kind = k64;
+    }
+  }
+  const T len = collide ? d : ds;
+  trace<T>(b, q, len, base);
+  for (int a = 0; a < 3; ++a) q.p[a] = q.p[a] + len * q.u[a];
+  if (collide) return kBoxCollide;
+  if (kind == 2) return kBoxLeak;
+  q.region ^= 1u;
+  return kBoxCross;
+}
+
+// One collision: implicit capture, group, direction, weight window.
+// Returns kBoxContinue, kBoxKilled (roulette), or the number n >= 2 of
+// particles of a split (the parent keeps weight w/n; the caller creates the
+// n-1 children from the parent's state after this call).
+template <int M, typename T>
+__device__ __forceinline__ int box_collide(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q) {
+  const uint32_t rg = q.region;
+  q.w = q.w * sel<T>(b.c[rg], b.c_f[rg]);
+  const double ug = r.next(l);
+  uint32_t g2 = q.g;
+  for (uint32_t k = q.g; k < b.ng; ++k) {
+    if (ug < b.cdf[rg][q.g][k]) {
+      g2 = k;
+      break;
+    }
+  }
+  q.g = g2;
+  iso_dir<M, T>(r, l, q.u);
+  set_inv(q);
+  const T wl = sel<T>(b.wl[rg], b.wl_f[rg]), wh = sel<T>(b.wh[rg], b.wh_f[rg]);
+  if (q.w < wl) {
+    const T ws = sel<T>(b.ws[rg], b.ws_f[rg]);
+    if (from_u<T>(r.next(l)) < q.w / ws) {
+      q.w = ws;
+      return kBoxContinue;
+    }
+    return kBoxKilled;
+  }
+  if (q.w > wh) {
+    const T nd = ceil(q.w / wh);
+    const uint32_t ns = nd > (T)b.max_split ? b.max_split : (uint32_t)nd;
+    if (ns > 1u) {
+      q.w = q.w / (T)ns;
+      return (int)ns + 8;  // encoded: n + 8 (> every other outcome)
+    }
+  }
+  return kBoxContinue;
+}
+
+constexpr int kSplitBase = 8;
+
+// Child k of a split: Eq. (5), S_c = hash(k, S_p) mod 2^m.
+__device__ __forceinline__ uint64_t child_seed(uint32_t k, uint64_t parent_state, uint64_t mask) {
+  return mcd::hash64((uint64_t)k, parent_state & mask) & mask;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_child(ChildRec& c, const Part<T>& q, uint64_t seed, uint32_t prob,
+                                            uint64_t tbase) {
+  for (int a = 0; a < 3; ++a) {
+    c.p[a] = (double)q.p[a];
+    c.u[a] = (double)q.u[a];
+  }
+  c.w = (double)q.w;
+  c.rng = seed;
+  c.tbase = tbase;
+  c.g = q.g;
+  c.region = q.region;
+  c.prob = prob;
+  c.pad = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_child(const ChildRec& c, Part<T>& q) {
+  for (int a = 0; a < 3; ++a) {
+    q.p[a] = (T)c.p[a];
+    q.u[a] = (T)c.u[a];
+  }
+  q.w = (T)c.w;
+  q.g = c.g;
+  q.region = c.region;
+  set_inv(q);
+}
+
+}  // namespace mcb

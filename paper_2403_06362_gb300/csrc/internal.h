@@ -53,6 +53,9 @@ struct mc_ctx {
   // Event-based schedule: particle bank and a pinned completion flag.
   mci::DeviceBuf bank;
   unsigned int* h_done = nullptr;
+  // Box transport: two banks of split children and a pinned count.
+  mci::DeviceBuf children;
+  unsigned long long* h_count = nullptr;
   // Private stream used only to capture graphs (the caller's stream may be
   // the legacy default stream, which cannot be captured).
   cudaStream_t capture_stream = nullptr;

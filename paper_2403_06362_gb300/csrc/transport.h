@@ -37,4 +37,40 @@ size_t slab_bank_bytes(uint32_t cap);
 int slab_event_run(const SlabLaunch& L, void* d_bank, uint32_t cap, unsigned int* h_done,
                    cudaStream_t capture_stream, cudaStream_t s);
 
+// One run of the box transport (box.cu history schedule, box_event.cu event
+// schedule).  Primaries are processed in chunks of primary_chunk; split
+// children wait in two device banks of child_cap records each
+// (generation ping-pong); d_child_count holds the two bank counts and
+// h_count is pinned host memory for reading them back.
+struct BoxLaunch {
+  const void* d_probs;
+  uint32_t n_problems;
+  uint32_t chunk;
+  uint64_t range_begin, total;
+  uint64_t primary_chunk;
+  unsigned long long* d_ticket;
+  void* d_child[2];
+  unsigned long long* d_child_count;
+  unsigned long long* h_count;
+  uint64_t child_cap;
+  const mc_tally* tally;
+  mc_lcg lcg;
+  uint64_t event_cap;
+  bool f32;
+  int block, blocks_per_sm, num_sms;
+  // event schedule only
+  void* d_bank;
+  uint32_t bank_cap;
+  unsigned int* h_done;
+  cudaStream_t capture_stream;
+};
+
+size_t box_dev_size();
+size_t box_child_rec_size();
+int box_fill_host(const mc_problem* src, uint32_t n, void* dst);
+int box_prep(void* d_probs, uint32_t n, cudaStream_t s);
+int box_history_run(const BoxLaunch& L, cudaStream_t s);
+size_t box_bank_bytes(uint32_t cap);
+int box_event_run(const BoxLaunch& L, cudaStream_t s);
+
 }  // namespace mci

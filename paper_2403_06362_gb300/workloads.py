@@ -162,3 +162,24 @@ def to_oracle_box(b, oracle):
     o.n_groups, o.mesh, o.max_split, o.n_batches = b["n_groups"], b["mesh"], b["max_split"], b["n_batches"]
     o.seeding, o.source = b["seeding"], b["source"]
     return o
+
+
+def to_mc_box(b, mc):
+    """dict -> (libmc mc_problem, mc_box_spec); keep the spec alive while the
+    problem is in use (the problem points to it)."""
+    spec = mc.mc_box_spec()
+    spec.side, spec.inner_lo, spec.inner_hi = b["side"], b["inner_lo"], b["inner_hi"]
+    for r in range(2):
+        spec.sigma_t[r], spec.c[r] = b["sigma_t"][r], b["c"][r]
+        spec.ww_low[r], spec.ww_high[r], spec.ww_survive[r] = b["ww_low"][r], b["ww_high"][r], b["ww_survive"][r]
+        for g in range(BOX_MAX_GROUPS):
+            for h in range(BOX_MAX_GROUPS):
+                spec.scatter_cdf[r][g][h] = b["cdf"][r, g, h]
+    spec.n_groups, spec.mesh, spec.max_split, spec.reserved = b["n_groups"], b["mesh"], b["max_split"], 0
+    import ctypes
+    prob = mc.mc_problem(geometry=mc.MC_GEOM_BOX, source=b["source"], seeding=b["seeding"],
+                         n_bins=b["mesh"] ** 3, n_batches=b["n_batches"], reserved=0, L=b["side"],
+                         sigma_t=b["sigma_t"][0], c=b["c"][0], n_histories=b["n_histories"], seed=b["seed"],
+                         stride_q=b["stride_q"], id_offset=b["id_offset"], key=b["key"],
+                         tally_offset=b["tally_offset"], box=ctypes.pointer(spec))
+    return prob, spec
