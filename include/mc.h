@@ -176,7 +176,8 @@ typedef struct {
 } mc_problem;
 
 typedef struct {
-    uint32_t schedule;      /* MC_SCHED_HISTORY, MC_SCHED_EVENT, MC_SCHED_AUTO    */
+    uint32_t schedule;      /* MC_SCHED_HISTORY, MC_SCHED_EVENT, MC_SCHED_AUTO     */
+                            /* (AUTO: the mc_autotune choice, cached per shape)   */
     uint32_t precision;     /* MC_FP64 or MC_FP32_GUARDED (flight and geometry)   */
     uint32_t block;         /* threads per block; 0 = library default             */
     uint32_t chunk;         /* histories a warp takes per ticket grab; 0 = 128    */
@@ -217,6 +218,21 @@ typedef struct {
 MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
                             uint32_t n_problems, const mc_run_config* config, const mc_tally* tally,
                             void* stream);
+
+/* Launch-shape autotuner for mc_transport_run (schedule MC_SCHED_AUTO calls
+ * it on the first run of each workload shape and caches the answer in the
+ * context).  Times every candidate -- history schedule with block 128/256/512
+ * and three chunk sizes, and the event schedule as a captured graph -- on a
+ * sample of the histories (all of them up to 2^16, else max(2^16, 1/8) from
+ * the middle of the list), writing only into a context-owned scratch tally;
+ * the caller's tally is not touched.  *best receives `base` with schedule,
+ * block, chunk and use_graph replaced by the fastest candidate; *best_ms
+ * (nullable) its time on the sample.  Results never depend on the choice:
+ * tallies are bit-identical across all candidates.  Synchronises `stream`.
+ * Errors: as mc_transport_run. */
+MC_API int mc_autotune(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                       const mc_run_config* base, const mc_tally* tally, mc_run_config* best, float* best_ms,
+                       void* stream);
 
 /* The slab transport of mc_transport_run for callers that cannot allocate
  * device memory (the paper has no counterpart; this is a deployment aid).

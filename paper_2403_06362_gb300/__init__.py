@@ -122,6 +122,16 @@ def mc_transport_run(ctx, lcg, problems, config, tally, stream=None):
                                            C.byref(tally), _stream(stream)))
 
 
+def mc_autotune(ctx, lcg, problems, base, tally, stream=None):
+    """Returns (best mc_run_config, its time in ms on the tuning sample)."""
+    arr = problems if isinstance(problems, C.Array) else problem_array(problems)
+    best = mc_run_config()
+    ms = C.c_float(0.0)
+    _ffi.check(lib().mc_autotune(ctx.handle, C.byref(lcg), arr, len(arr), C.byref(base), C.byref(tally),
+                                 C.byref(best), C.byref(ms), _stream(stream)))
+    return best, float(ms.value)
+
+
 def mc_transport_run_static(lcg, problems, config, tally, stream=None):
     """mc_transport_run without a context: scratch lives in a fixed device
     array inside libmc (for callers that cannot allocate device memory)."""

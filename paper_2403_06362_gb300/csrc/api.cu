@@ -9,7 +9,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstddef>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -78,6 +80,28 @@ namespace {
 // Layout of the small scratch block.
 constexpr size_t kTicketOff = 0;     // unsigned long long ticket
 constexpr size_t kScratchBytes = 256;
+
+// Host half of staging: waits until the pinned buffer is free, sizes the
+// buffers and writes the problem records into pinned memory.
+int stage_host(mc_ctx* ctx, const mc_problem* problems, uint32_t n, size_t* bytes_out) {
+  const bool box = problems[0].geometry == MC_GEOM_BOX;
+  const size_t bytes = (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
+  if (ctx->staged) MC_TRY_CUDA(cudaEventSynchronize(ctx->staged));
+  if (bytes > ctx->h_problems_bytes) {
+    if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
+    ctx->h_problems = nullptr;
+    ctx->h_problems_bytes = 0;
+    MC_TRY_CUDA(cudaMallocHost(&ctx->h_problems, bytes));
+    ctx->h_problems_bytes = bytes;
+  }
+  int st = ctx->problems.reserve(bytes);
+  if (st != MC_OK) return st;
+  if (box) mci::box_fill_host(problems, n, ctx->h_problems);
+  else mci::slab_fill_host(problems, n, ctx->h_problems);
+  if (!ctx->staged) MC_TRY_CUDA(cudaEventCreateWithFlags(&ctx->staged, cudaEventDisableTiming));
+  *bytes_out = bytes;
+  return MC_OK;
+}
 
 int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStream_t s) {
   const bool box = problems[0].geometry == MC_GEOM_BOX;
@@ -232,6 +256,7 @@ MC_API int mc_ctx_create(mc_ctx** out, int device) {
   MC_TRY_CUDA(cudaSetDevice(device));
   mc_ctx* c = new mc_ctx();
   c->device = device;
+  c->tune_cache = new std::unordered_map<uint64_t, mc_run_config>();
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -263,50 +288,50 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   if (ctx->h_done) cudaFreeHost(ctx->h_done);
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   ctx->children.release();
+  ctx->tune_tally.release();
+  delete ctx->tune_cache;
+  if (ctx->graphs) {
+    for (auto& kv : ctx->graphs->m) cudaGraphExecDestroy(kv.second);
+    delete ctx->graphs;
+  }
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   delete ctx;
 }
 
 MC_API uint64_t mc_hash64(uint64_t k, uint64_t s) { return mcd::hash64(k, s); }
 
-MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
-                            uint32_t n_problems, const mc_run_config* cfg, const mc_tally* tally,
-                            void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Validates a call; returns the total history count in *total.
+int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                 const mc_run_config* cfg, const mc_tally* tally, uint64_t* total) {
   if (!ctx || !problems || n_problems == 0 || !cfg || !tally || !tally->d_bins || !tally->d_counts) {
     mci::set_error("mc_transport_run: NULL argument or no problems");
     return MC_ERR_ARG;
   }
   int st = mci::check_lcg(lcg);
   if (st != MC_OK) return st;
-  uint64_t total = 0;
-  st = check_problems(problems, n_problems, tally, &total);
+  st = check_problems(problems, n_problems, tally, total);
   if (st != MC_OK) return st;
   if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
       (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512))) {
     mci::set_error("mc_transport_run: bad run config (schedule/precision/tally_mode/block)");
     return MC_ERR_ARG;
   }
-  const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? total : cfg->range_end;
-  if (rb > re || re > total) {
+  const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? *total : cfg->range_end;
+  if (rb > re || re > *total) {
     mci::set_error("mc_transport_run: range [%llu, %llu) outside the %llu histories", (unsigned long long)rb,
-                   (unsigned long long)re, (unsigned long long)total);
+                   (unsigned long long)re, (unsigned long long)*total);
     return MC_ERR_ARG;
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+  return MC_OK;
+}
 
-  st = stage_problems(ctx, problems, n_problems, s);
-  if (st != MC_OK) return st;
-  if (!cfg->accumulate) {
-    MC_TRY_CUDA(cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), s));
-    MC_TRY_CUDA(cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), s));
-  }
-  auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
-  MC_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-  if (re == rb) return MC_OK;
-
-  if (problems[0].geometry == MC_GEOM_BOX) return run_box(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, s);
-
+int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_config* cfg,
+                     const mc_tally* tally, uint64_t rb, uint64_t re, unsigned long long* ticket,
+                     mci::SlabLaunch* out) {
   mci::SlabLaunch L{};
   L.d_probs = ctx->problems.ptr;
   L.n_problems = n_problems;
@@ -330,6 +355,95 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
   L.block = cfg->block ? (int)cfg->block : 256;
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
+  *out = L;
+  return MC_OK;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n);
+
+// History schedule as one CUDA graph per launch shape: problem upload from
+// the pinned staging buffer, prep kernel, memsets and the persistent kernel
+// are captured once; later calls refresh the pinned records and replay.
+int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                   const mc_run_config* cfg, const mc_tally* tally, uint64_t rb, uint64_t re, cudaStream_t s) {
+  size_t bytes = 0;
+  int st = stage_host(ctx, problems, n_problems, &bytes);
+  if (st != MC_OK) return st;
+  auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
+  mci::SlabLaunch L{};
+  st = make_slab_launch(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, &L);
+  if (st != MC_OK) return st;
+  uint64_t key = 1469598103934665603ull;
+  const void* ptrs[] = {ctx->problems.ptr, ctx->h_problems, tally->d_bins, tally->d_counts, tally->d_hist_state,
+                        tally->d_hist_draws};
+  key = fnv(key, ptrs, sizeof ptrs);
+  key = fnv(key, cfg, sizeof *cfg);
+  key = fnv(key, lcg, sizeof *lcg);
+  key = fnv(key, &n_problems, sizeof n_problems);
+  key = fnv(key, &bytes, sizeof bytes);
+  key = fnv(key, &tally->n_slots, sizeof tally->n_slots);
+  if (!ctx->graphs) ctx->graphs = new mci::GraphCache();
+  auto it = ctx->graphs->m.find(key);
+  cudaGraphExec_t exec = nullptr;
+  if (it != ctx->graphs->m.end()) {
+    exec = it->second;
+  } else {
+    if (!ctx->capture_stream) MC_TRY_CUDA(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    if (ctx->graphs->m.size() >= 16) {
+      for (auto& kv : ctx->graphs->m) cudaGraphExecDestroy(kv.second);
+      ctx->graphs->m.clear();
+    }
+    cudaStream_t cs = ctx->capture_stream;
+    cudaGraph_t g = nullptr;
+    MC_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, cs);
+    mci::slab_prep(ctx->problems.ptr, n_problems, cs);
+    if (!cfg->accumulate) {
+      cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), cs);
+      cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), cs);
+    }
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), cs);
+    const int lst = mci::slab_history_launch(L, cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (lst != MC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return lst;
+    }
+    if (e != cudaSuccess) return mci::cuda_status(e, "cudaStreamEndCapture(history run)");
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return mci::cuda_status(e, "cudaGraphInstantiate(history run)");
+    ctx->graphs->m[key] = exec;
+  }
+  MC_TRY_CUDA(cudaGraphLaunch(exec, s));
+  MC_TRY_CUDA(cudaEventRecord(ctx->staged, s));
+  return MC_OK;
+}
+
+// Runs a validated call whose schedule is HISTORY or EVENT.
+int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                       const mc_run_config* cfg, const mc_tally* tally, uint64_t total, cudaStream_t s) {
+  int st = MC_OK;
+  const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? total : cfg->range_end;
+  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+  if (cfg->use_graph && cfg->schedule == MC_SCHED_HISTORY && problems[0].geometry == MC_GEOM_SLAB && re > rb)
+    return run_slab_graph(ctx, lcg, problems, n_problems, cfg, tally, rb, re, s);
+
+  st = stage_problems(ctx, problems, n_problems, s);
+  if (st != MC_OK) return st;
+  if (!cfg->accumulate) {
+    MC_TRY_CUDA(cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), s));
+    MC_TRY_CUDA(cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), s));
+  }
+  auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
+  MC_TRY_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+  if (re == rb) return MC_OK;
+
+  if (problems[0].geometry == MC_GEOM_BOX) return run_box(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, s);
+
+  mci::SlabLaunch L{};
+  st = make_slab_launch(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, &L);
+  if (st != MC_OK) return st;
   if (cfg->schedule == MC_SCHED_EVENT) {
     // Bank of up to 2^20 particles (about 100 MiB); allocated on first use.
     const uint32_t cap = (uint32_t)std::min<uint64_t>(L.total, 1u << 20);
@@ -342,6 +456,140 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
                                s);
   }
   return mci::slab_history_launch(L, s);
+}
+
+// FNV-1a over the bytes that decide the best launch shape.
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+uint64_t tune_key(const mc_problem* problems, uint32_t n, const mc_run_config* cfg, const mc_tally* tally,
+                  uint64_t total) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv(h, &n, sizeof n);
+  h = fnv(h, &total, sizeof total);
+  h = fnv(h, &cfg->precision, sizeof cfg->precision);
+  h = fnv(h, &cfg->tally_mode, sizeof cfg->tally_mode);
+  h = fnv(h, &tally->n_slots, sizeof tally->n_slots);
+  for (uint32_t i = 0; i < n; ++i) {
+    const mc_problem& q = problems[i];
+    h = fnv(h, &q, offsetof(mc_problem, box));
+    if (q.box) h = fnv(h, q.box, sizeof(mc_box_spec));
+  }
+  return h;
+}
+
+int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                  const mc_run_config* base, const mc_tally* tally, uint64_t total, mc_run_config* best,
+                  float* best_ms, cudaStream_t s) {
+  // Scratch tally: the caller's tally is never written while tuning.
+  const size_t bins = tally->n_slots * sizeof(int64_t), cnts = (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t);
+  int st = ctx->tune_tally.reserve(bins + cnts);
+  if (st != MC_OK) return st;
+  mc_tally t2{};
+  t2.d_bins = static_cast<int64_t*>(ctx->tune_tally.ptr);
+  t2.n_slots = tally->n_slots;
+  t2.d_counts = reinterpret_cast<uint64_t*>(static_cast<char*>(ctx->tune_tally.ptr) + bins);
+  // A sample from the middle of the concatenated history list.
+  const uint64_t S = total <= (1ull << 16) ? total : std::max<uint64_t>(1ull << 16, total / 8);
+  const uint64_t start = (total - S) / 2;
+  struct Cand { uint32_t schedule, block, chunk, graph; };
+  const bool box = problems[0].geometry == MC_GEOM_BOX;
+  std::vector<Cand> cands;
+  for (uint32_t b : {128u, 256u, 512u})
+    for (uint32_t c : box ? std::vector<uint32_t>{32u, 64u, 256u} : std::vector<uint32_t>{32u, 128u, 512u})
+      cands.push_back({MC_SCHED_HISTORY, b, c, 0u});
+  cands.push_back({MC_SCHED_EVENT, 256u, 0u, 1u});
+  cudaEvent_t e0, e1;
+  MC_TRY_CUDA(cudaEventCreate(&e0));
+  MC_TRY_CUDA(cudaEventCreate(&e1));
+  float best_t = 0.0f;
+  bool have = false;
+  for (const Cand& c : cands) {
+    mc_run_config r = *base;
+    r.schedule = c.schedule;
+    r.block = c.block;
+    r.chunk = c.chunk;
+    r.use_graph = c.graph;
+    r.accumulate = 0;
+    r.range_begin = start;
+    r.range_end = start + S;
+    st = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);  // warm-up
+    if (st == MC_OK) st = mci::cuda_status(cudaEventRecord(e0, s), "cudaEventRecord");
+    if (st == MC_OK) st = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);
+    if (st == MC_OK) st = mci::cuda_status(cudaEventRecord(e1, s), "cudaEventRecord");
+    if (st == MC_OK) st = mci::cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    if (st != MC_OK) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (!have || ms < best_t) {
+      best_t = ms;
+      *best = r;
+      have = true;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != MC_OK) return st;
+  best->range_begin = base->range_begin;
+  best->range_end = base->range_end;
+  best->accumulate = base->accumulate;
+  if (best_ms) *best_ms = best_t;
+  (*ctx->tune_cache)[tune_key(problems, n_problems, base, tally, total)] = *best;
+  return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
+                            uint32_t n_problems, const mc_run_config* cfg, const mc_tally* tally,
+                            void* stream) {
+  uint64_t total = 0;
+  int st = validate_run(ctx, lcg, problems, n_problems, cfg, tally, &total);
+  if (st != MC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cfg->schedule != MC_SCHED_AUTO) return transport_run_impl(ctx, lcg, problems, n_problems, cfg, tally, total, s);
+  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+  mc_run_config r{};
+  auto it = ctx->tune_cache->find(tune_key(problems, n_problems, cfg, tally, total));
+  if (it != ctx->tune_cache->end()) {
+    r = it->second;
+  } else {
+    st = autotune_impl(ctx, lcg, problems, n_problems, cfg, tally, total, &r, nullptr, s);
+    if (st != MC_OK) return st;
+  }
+  r.range_begin = cfg->range_begin;
+  r.range_end = cfg->range_end;
+  r.accumulate = cfg->accumulate;
+  r.event_cap = cfg->event_cap;
+  return transport_run_impl(ctx, lcg, problems, n_problems, &r, tally, total, s);
+}
+
+MC_API int mc_autotune(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                       const mc_run_config* base, const mc_tally* tally, mc_run_config* best, float* best_ms,
+                       void* stream) {
+  uint64_t total = 0;
+  int st = validate_run(ctx, lcg, problems, n_problems, base, tally, &total);
+  if (st != MC_OK) return st;
+  if (!best) {
+    mci::set_error("mc_autotune: best is NULL");
+    return MC_ERR_ARG;
+  }
+  if (total == 0) {
+    *best = *base;
+    best->schedule = MC_SCHED_HISTORY;
+    if (best_ms) *best_ms = 0.0f;
+    return MC_OK;
+  }
+  MC_TRY_CUDA(cudaSetDevice(ctx->device));
+  return autotune_impl(ctx, lcg, problems, n_problems, base, tally, total, best, best_ms, (cudaStream_t)stream);
 }
 
 MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t problem, const mc_tally* tally,

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <unordered_map>
 
 #include "../../include/mc.h"
 
@@ -34,7 +35,10 @@ struct DeviceBuf {
   void release();
 };
 
-struct GraphCache;  // transport launch graphs keyed by shape
+// Instantiated launch graphs of the history schedule, keyed by launch shape.
+struct GraphCache {
+  std::unordered_map<uint64_t, cudaGraphExec_t> m;
+};
 
 }  // namespace mci
 
@@ -60,4 +64,7 @@ struct mc_ctx {
   // the legacy default stream, which cannot be captured).
   cudaStream_t capture_stream = nullptr;
   mci::GraphCache* graphs = nullptr;
+  // Autotuner: scratch tally and the best configuration per workload shape.
+  mci::DeviceBuf tune_tally;
+  std::unordered_map<uint64_t, mc_run_config>* tune_cache = nullptr;
 };

@@ -103,3 +103,11 @@ def test_box_fp32_error_stated(env, oracle):
     assert abs(g - e) / e < 2e-2
     c = counts_of(t32)
     assert int(c[0]) + int(c[14]) == int(c[6]) + int(c[11]) + int(c[12])
+
+
+def test_box_auto_schedule_matches(env):
+    b = W.box_problem(n_histories=30_000)
+    ref = gpu_box(env, b, hist=False)
+    auto = gpu_box(env, b, hist=False, schedule=2)
+    assert np.array_equal(ref.bins.cpu().numpy(), auto.bins.cpu().numpy())
+    assert np.array_equal(counts_of(ref), counts_of(auto))

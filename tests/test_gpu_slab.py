@@ -225,3 +225,36 @@ def test_event_schedule_event_cap_and_ranges(env):
     a, _ = gpu_run(env, probs, range_begin=123, range_end=4567)
     b, _ = gpu_run(env, probs, range_begin=123, range_end=4567, schedule=1)
     _same_bits(a, b, 1)
+
+
+def test_autotune_leaves_tally_alone_and_auto_matches(env):
+    mc, ctx, torch = env
+    probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=40, max_histories=20_000)
+    cprobs = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    tally = mc.Tally(W.tally_slots(probs), len(probs))
+    tally.bins.fill_(12345)
+    best, ms = mc.mc_autotune(ctx, mc.make_lcg(), cprobs, mc.mc_run_config(), tally.c)
+    torch.cuda.synchronize()
+    assert int(tally.bins.min()) == 12345 and int(tally.bins.max()) == 12345
+    assert ms > 0 and best.schedule in (0, 1) and best.block in (128, 256, 512)
+    ref, _ = gpu_run(env, probs, n_hist_out=False)
+    auto, _ = gpu_run(env, probs, n_hist_out=False, schedule=2)
+    again, _ = gpu_run(env, probs, n_hist_out=False, schedule=2)
+    _same_bits(ref, auto, len(probs))
+    _same_bits(ref, again, len(probs))
+
+
+def test_history_graph_replay_with_new_problem_data(env):
+    mc, ctx, torch = env
+    a = W.slab_batched(W.SEED_HASH_HIER, n_problems=16, max_histories=5000, seed=7)
+    b = W.slab_batched(W.SEED_HASH_HIER, n_problems=16, max_histories=5000, seed=8)
+    # same shape (count, totals differ -> force equal totals by capping all)
+    for p in a + b:
+        p["n_histories"] = 5000
+    tally = mc.Tally(W.tally_slots(a), len(a), n_histories=16 * 5000)
+    for probs in (a, b, a):
+        cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+        mc.mc_transport_run(ctx, mc.make_lcg(), cp, mc.mc_run_config(use_graph=1), tally.c)
+        torch.cuda.synchronize()
+        ref, _ = gpu_run(env, probs)
+        _same_bits(ref, tally, len(probs))
