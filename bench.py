@@ -221,7 +221,14 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
+    ap.add_argument("--profile-workload", default=None,
+                    choices=["slab_long_fp64", "slab_long_fp32", "slab_small_fp64", "box_fp32", "box_fp64",
+                             "batched_fp32"],
+                    help="run one transport workload (a warm-up run, then one run) and exit; for profilers")
+    ap.add_argument("--histories", type=int, default=0, help="history count for --profile-workload")
     args = ap.parse_args()
+    if args.profile_workload:
+        return profile_workload(args)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
@@ -353,6 +360,49 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def profile_workload(args):
+    """One transport workload, run twice (warm-up + measured), for ncu."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import workloads as W
+    ctx = mc.Context(0)
+    lcg = mc.make_lcg()
+    name = args.profile_workload
+    keep = None
+    if name.startswith("box"):
+        b = W.box_large(W.SEED_HASH, n_histories=args.histories or 10**6)
+        prob, keep = W.to_mc_box(b, mc)
+        cp = mc.problem_array([prob])
+        tally = mc.Tally(W.box_tally_slots(b), 1)
+        n = b["n_histories"]
+    else:
+        if name.startswith("slab_long"):
+            probs = W.slab_long(W.SEED_HASH, n_histories=args.histories or 10**5)
+        elif name.startswith("slab_small"):
+            probs = W.slab_small(W.SEED_HASH, n_histories=args.histories or 10**4)
+        else:
+            probs = W.slab_batched(W.SEED_HASH_HIER)
+        cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+        tally = mc.Tally(W.tally_slots(probs), len(probs))
+        n = sum(p["n_histories"] for p in probs)
+    cfg = mc.mc_run_config(precision=1 if "fp32" in name else 0)
+    times = []
+    for _ in range(2):
+        a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c)
+        b2.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b2))
+    r = mc.mc_tally_read(ctx, cp, 0, tally.c, check=False)
+    print(json.dumps({"workload": name, "histories": n, "ms": times[-1], "flights": r.counts["flights"]}))
+    del keep
+    ctx.close()
+
+
 def seeding_detail(mc, ctx, lcg, torch, dev, stream):
     """Seeding only (mc_seed_hash / mc_seed_stride), HBM-store bound:
     8 bytes written per stream."""
@@ -381,14 +431,21 @@ def seeding_detail(mc, ctx, lcg, torch, dev, stream):
 
 
 def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
-    """Slab transport histories/s: the 10^4-history slab, the 10^6-history
-    long-chain slab (fp64 and fp32-guarded, hash and stride), and the 256
-    batched problems (one fp32 launch vs one fp64 launch per problem)."""
+    """Transport throughput on the slab and box workloads (histories/s), the
+    batched slab problems (one fp32 launch vs the plain fp64 single-problem
+    loop), history vs event schedules with a bit-identity check, and the
+    Section 5 normality procedure on the batch means, hash vs stride."""
     res = {}
 
-    def timed(probs, reps=2, **cfgkw):
-        tally = mc.Tally(W.tally_slots(probs), len(probs))
-        cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    def timed(probs, reps=2, box=None, keep=False, **cfgkw):
+        if box is not None:
+            prob, spec = W.to_mc_box(box, mc)
+            cp = mc.problem_array([prob])
+            tally = mc.Tally(W.box_tally_slots(box), 1)
+            tally._keep = spec
+        else:
+            cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+            tally = mc.Tally(W.tally_slots(probs), len(probs))
         cfg = mc.mc_run_config(**cfgkw)
         mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
         torch.cuda.synchronize()
@@ -403,40 +460,82 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             best = ms if best is None else min(best, ms)
         return best, tally, cp
 
-    for name, probs in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
-        for sname, s in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
+    def entry(ms, tally, cp, n, idx=0):
+        r = mc.mc_tally_read(ctx, cp, idx, tally.c, stream, check=False)
+        return {"ms": ms, "histories_per_s": n / (ms / 1e3), "flights_per_s": r.counts["flights"] / (ms / 1e3),
+                "exceed_hist": r.counts["exceed_hist"], "max_draws": r.counts["max_draws"]}
+
+    for name, fn in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
+        for sname, sd in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
+            p = fn(sd)
+            n = p[0]["n_histories"]
             for prec in (0, 1):
-                p = probs(s)
                 ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, precision=prec)
-                key = f"{name}_{sname}_{'fp32' if prec else 'fp64'}"
-                r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
-                res[key] = {"ms": ms, "histories_per_s": p[0]["n_histories"] / (ms / 1e3),
-                            "flights_per_s": r.counts["flights"] / (ms / 1e3),
-                            "exceed_hist": r.counts["exceed_hist"], "max_draws": r.counts["max_draws"]}
+                res[f"{name}_{sname}_{'fp32' if prec else 'fp64'}"] = entry(ms, tally, cp, n)
+                if prec == 0:
+                    hist_bins = tally.bins.clone()
+            ms, tally, cp = timed(p, reps=1, precision=0, schedule=1, use_graph=1)
+            e = entry(ms, tally, cp, n)
+            e["bits_identical_to_history"] = bool(torch.equal(tally.bins, hist_bins))
+            res[f"{name}_{sname}_fp64_event"] = e
+
+    # Section 5: normality of the batch means, per bin, hash vs stride
+    norm = {}
+    for name, fn in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
+        for sname, sd in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
+            p = fn(sd)
+            _, tally, cp = timed(p, reps=0, precision=0)
+            r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream)
+            _, wv, pv = mc.mc_normality(r.batch)
+            norm[f"{name}_{sname}"] = {"batches": int(r.batch.shape[0]), "points": int(r.batch.shape[1]),
+                                       "fails_p_lt_0.05": int(np.sum(pv < 0.05)),
+                                       "min_p": float(np.min(pv)), "median_p": float(np.median(pv))}
+    res["normality"] = norm
+
+    # 256 batched slab problems
     probs = W.slab_batched(W.SEED_HASH_HIER)
     nh = sum(p["n_histories"] for p in probs)
     ms32, _, _ = timed(probs, reps=2, precision=1)
+    ms32g, _, _ = timed(probs, reps=2, precision=1, use_graph=1)
+    ms32a, _, _ = timed(probs, reps=2, precision=1, schedule=2)
     ms64, _, _ = timed(probs, reps=1, precision=0)
-    # the plain fp64 single-problem path: one launch per problem
-    t0 = time.perf_counter()
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tallies = []
+    singles = []
     for p in probs:
         q = dict(p)
         q["tally_offset"] = 0
-        tallies.append((mc.Tally(W.tally_slots([q]), 1), mc.problem_array([W.to_mc_problem(q, mc)])))
+        singles.append((mc.Tally(W.tally_slots([q]), 1), mc.problem_array([W.to_mc_problem(q, mc)])))
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for tl, cp in tallies:
+    for tl, cp in singles:
         mc.mc_transport_run(ctx, lcg, cp, mc.mc_run_config(), tl.c, stream)
     b.record(stream)
     torch.cuda.synchronize()
     ms_single = a.elapsed_time(b)
-    _ = t0
-    res["slab_batched"] = {"histories": nh, "ms_batched_fp32": ms32, "ms_batched_fp64": ms64,
+    best32 = min(ms32, ms32g, ms32a)
+    res["slab_batched"] = {"histories": nh, "ms_batched_fp32": ms32, "ms_batched_fp32_graph": ms32g,
+                           "ms_batched_fp32_autotuned": ms32a, "ms_batched_fp64": ms64,
                            "ms_single_fp64_loop": ms_single,
-                           "histories_per_s_batched_fp32": nh / (ms32 / 1e3),
-                           "speedup_batched_fp32_over_single_fp64": ms_single / ms32}
+                           "histories_per_s_batched_fp32": nh / (best32 / 1e3),
+                           "speedup_batched_fp32_over_single_fp64": ms_single / best32}
+
+    # 3D two-region box, 10^8 source histories
+    box = W.box_large(W.SEED_HASH)
+    n = box["n_histories"]
+    bits = {}
+    for label, kw in (("fp32_history", dict(precision=1)), ("fp32_event", dict(precision=1, schedule=1, use_graph=1)),
+                      ("fp64_history", dict(precision=0)), ("fp64_event", dict(precision=0, schedule=1, use_graph=1))):
+        ms, tally, cp = timed(None, reps=1, box=box, **kw)
+        e = entry(ms, tally, cp, n)
+        r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
+        e.update(children=r.counts["children"], splits=r.counts["splits"], roulette_kills=r.counts["roulette_kills"])
+        bits[label] = tally.bins.clone()
+        res[f"box_large_hash_{label}"] = e
+    res["box_large_hash_fp32_event"]["bits_identical_to_history"] = bool(torch.equal(bits["fp32_event"],
+                                                                                      bits["fp32_history"]))
+    res["box_large_hash_fp64_event"]["bits_identical_to_history"] = bool(torch.equal(bits["fp64_event"],
+                                                                                      bits["fp64_history"]))
+    del bits
     return res
 
 

@@ -206,7 +206,7 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
   mci::BoxLaunch L{};
   L.d_probs = ctx->problems.ptr;
   L.n_problems = n_problems;
-  L.chunk = cfg->chunk ? cfg->chunk : 64u;
+  L.chunk = cfg->chunk ? cfg->chunk : 32u;
   L.range_begin = rb;
   L.total = re - rb;
   L.primary_chunk = kPrimaryChunk;
@@ -222,7 +222,8 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
   // the default cap of 2^22 flights per particle only bounds pathologies.
   L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 22);
   L.f32 = cfg->precision == MC_FP32_GUARDED;
-  L.block = cfg->block ? (int)cfg->block : 256;
+  // the box kernel is built for at most 256 threads per block (3 blocks per SM)
+  L.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 256;
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
   if (cfg->schedule == MC_SCHED_EVENT) {
@@ -335,7 +336,11 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const 
   mci::SlabLaunch L{};
   L.d_probs = ctx->problems.ptr;
   L.n_problems = n_problems;
-  L.chunk = cfg->chunk ? cfg->chunk : 128u;
+  // Default chunk: about four grabs per resident warp (fine-grained enough to
+  // balance long-tailed histories, coarse enough that lanes rarely change
+  // problem in a batched launch), within [32, 256].
+  L.chunk = cfg->chunk ? cfg->chunk
+                       : (uint32_t)std::min<uint64_t>(256, std::max<uint64_t>(32, (re - rb) / ((uint64_t)ctx->num_sms * 256)));
   L.range_begin = rb;
   L.total = re - rb;
   L.d_ticket = ticket;
@@ -501,8 +506,8 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
   struct Cand { uint32_t schedule, block, chunk, graph; };
   const bool box = problems[0].geometry == MC_GEOM_BOX;
   std::vector<Cand> cands;
-  for (uint32_t b : {128u, 256u, 512u})
-    for (uint32_t c : box ? std::vector<uint32_t>{32u, 64u, 256u} : std::vector<uint32_t>{32u, 128u, 512u})
+  for (uint32_t b : box ? std::vector<uint32_t>{128u, 256u} : std::vector<uint32_t>{128u, 256u, 512u})
+    for (uint32_t c : {8u, 32u, 128u})
       cands.push_back({MC_SCHED_HISTORY, b, c, 0u});
   cands.push_back({MC_SCHED_EVENT, 256u, 0u, 1u});
   cudaEvent_t e0, e1;

@@ -112,13 +112,21 @@ __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64
 }
 
 template <int M, typename T>
-__global__ void __launch_bounds__(512) box_history_kernel(const BoxArgs a) {
+__global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
   __shared__ mcd::Affine tab[64];
+  // A single problem's record is read on every flight: keep it in shared memory.
+  __shared__ __align__(16) unsigned char s_prob[sizeof(BoxDev)];
   if (threadIdx.x == 0) {
     mcd::Affine sq{a.lcg.g, a.lcg.c};
     for (int j = 0; j < 64; ++j) { tab[j] = sq; sq = mcd::compose(sq, sq); }
   }
+  if (a.nprob == 1) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(a.probs);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(s_prob);
+    for (uint32_t i = threadIdx.x; i < sizeof(BoxDev) / 8; i += blockDim.x) dst[i] = src[i];
+  }
   __syncthreads();
+  const BoxDev* probs = a.nprob == 1 ? reinterpret_cast<const BoxDev*>(s_prob) : a.probs;
   const unsigned kFull = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -129,7 +137,7 @@ __global__ void __launch_bounds__(512) box_history_kernel(const BoxArgs a) {
   BoxCounts lc;
   lc.prob = -1;
   lc.clear();
-  const BoxDev* P = a.probs;
+  const BoxDev* P = probs;
   uint32_t pi = 0;
   mcs::Rng<M> r{0ull, 0ull};
   mcb::Part<T> q{};
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(512) box_history_kernel(const BoxArgs a) {
         if (a.child_in == nullptr) {
           gi = a.range_begin + item;
           pi = a.nprob == 1 ? 0u : find_box(a.probs, a.nprob, gi);
-          P = a.probs + pi;
+          P = probs + pi;
           const uint64_t id = gi - P->hist_begin;
           const uint64_t nvox = (uint64_t)P->mesh * P->mesh * P->mesh;
           tbase = P->tally_offset + mcs::batch_of(id, P->n_hist, P->n_batches) * nvox;
@@ -167,7 +175,7 @@ __global__ void __launch_bounds__(512) box_history_kernel(const BoxArgs a) {
         } else {
           const ChildRec c = a.child_in[item];
           pi = c.prob;
-          P = a.probs + pi;
+          P = probs + pi;
           tbase = c.tbase;
           r = mcs::Rng<M>{c.rng, 0ull};
           mcb::load_child<T>(c, q);

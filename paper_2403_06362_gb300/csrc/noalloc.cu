@@ -153,7 +153,7 @@ extern "C" MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_proble
   mci::SlabLaunch L{};
   L.d_probs = dprobs;
   L.n_problems = n_problems;
-  L.chunk = cfg->chunk ? cfg->chunk : 128u;
+  L.chunk = cfg->chunk ? cfg->chunk : 32u;
   L.range_begin = rb;
   L.total = re - rb;
   L.d_ticket = ticket;
