@@ -258,3 +258,12 @@ def test_history_graph_replay_with_new_problem_data(env):
         torch.cuda.synchronize()
         ref, _ = gpu_run(env, probs)
         _same_bits(ref, tally, len(probs))
+
+
+def test_tally_overflow_reported(env):
+    mc, ctx, torch = env
+    probs = W.slab_small(W.SEED_HASH, n_histories=100)
+    tally, cprobs = gpu_run(env, probs, n_hist_out=False)
+    tally.bins[7] = 2**62  # a bin at the headroom limit
+    r = mc.mc_tally_read(ctx, cprobs, 0, tally.c, check=False)
+    assert r.status == mc._ffi.MC_ERR_OVERFLOW
