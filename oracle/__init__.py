@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mc_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "mc_oracle_box.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "mc_oracle_box.c"), os.path.join(_HERE, "mc_oracle_azurv1.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 NCOUNT = 16
@@ -62,6 +62,16 @@ class BoxProblem(C.Structure):
         ("id_offset", C.c_uint64), ("key", C.c_uint64), ("tally_offset", C.c_uint64),
         ("n_groups", C.c_uint32), ("mesh", C.c_uint32), ("max_split", C.c_uint32),
         ("n_batches", C.c_uint32), ("seeding", C.c_uint32), ("source", C.c_uint32),
+    ]
+
+
+class Azurv1Problem(C.Structure):
+    _fields_ = [
+        ("c", C.c_double), ("nu", C.c_double), ("t_end", C.c_double), ("x_half", C.c_double),
+        ("sigma_t", C.c_double),
+        ("seed", C.c_uint64), ("stride_q", C.c_uint64), ("id_offset", C.c_uint64), ("tally_offset", C.c_uint64),
+        ("n_reps", C.c_uint32), ("n_batches", C.c_uint32), ("per_batch", C.c_uint32),
+        ("n_time_bins", C.c_uint32), ("seeding", C.c_uint32), ("pad", C.c_uint32),
     ]
 
 
@@ -114,6 +124,10 @@ def lib():
             L.or_box_trace.restype = None; L.or_box_trace.argtypes = [BP, P, P, dbl, dbl, P, P]
             L.or_box_surface_dist.restype = dbl
             L.or_box_surface_dist.argtypes = [BP, P, P, u32, C.POINTER(C.c_int)]
+            AP = C.POINTER(Azurv1Problem)
+            L.or_azurv1_seed.restype = u64; L.or_azurv1_seed.argtypes = [C.POINTER(Lcg), AP, u64]
+            L.or_azurv1_run.restype = C.c_int
+            L.or_azurv1_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, P, P]
             L.or_norm_cdf.restype = dbl; L.or_norm_cdf.argtypes = [dbl]
             L.or_norm_ppf.restype = dbl; L.or_norm_ppf.argtypes = [dbl]
             L.or_shapiro_wilk.restype = C.c_int
@@ -327,3 +341,27 @@ def box_surface_dist(prob: BoxProblem, p, u, region):
     k = C.c_int(0)
     d = float(lib().or_box_surface_dist(C.byref(prob), _ptr(p), _ptr(u), region, C.byref(k)))
     return d, int(k.value)
+
+
+# --- the paper's supercritical time-dependent problem (mc_oracle_azurv1.c) -------
+
+def azurv1_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, event_cap=2**62, tally=None,
+               counts=None, per_history=False):
+    total = int(prob.n_reps) * int(prob.n_batches) * int(prob.per_batch)
+    if g_end is None:
+        g_end = total
+    size = int(prob.tally_offset) + int(prob.n_reps) * int(prob.n_batches) * int(prob.n_time_bins)
+    if tally is None:
+        tally = np.zeros(size, dtype=np.int64)
+    if counts is None:
+        counts = np.zeros(NCOUNT, dtype=np.uint64)
+    n = g_end - g_begin
+    hs = np.zeros(n, dtype=np.uint64) if per_history else None
+    hd = np.zeros(n, dtype=np.uint64) if per_history else None
+    st = lib().or_azurv1_run(C.byref(lcg), C.byref(prob), g_begin, g_end, event_cap, _ptr(tally),
+                             _ptr(counts), _ptr(hs), _ptr(hd))
+    return dict(status=st, tally=tally, counts=counts, hist_state=hs, hist_draws=hd)
+
+
+def azurv1_seed(lcg: Lcg, prob: Azurv1Problem, g: int) -> int:
+    return int(lib().or_azurv1_seed(C.byref(lcg), C.byref(prob), g))

@@ -97,6 +97,19 @@ void or_box_trace(const or_box_problem* b, const double* p, const double* u, dou
 double or_box_surface_dist(const or_box_problem* b, const double* p, const double* u, uint32_t region,
                            int* kind_out);
 
+/* The paper's supercritical time-dependent problem (mc_oracle_azurv1.c). */
+typedef struct {
+    double c, nu, t_end, x_half, sigma_t;
+    uint64_t seed, stride_q, id_offset, tally_offset;
+    uint32_t n_reps, n_batches, per_batch, n_time_bins;
+    uint32_t seeding, pad;
+} or_azurv1_problem;
+
+uint64_t or_azurv1_seed(const or_lcg* l, const or_azurv1_problem* a, uint64_t g);
+int or_azurv1_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
+                  uint64_t event_cap, int64_t* tally, uint64_t* counts, uint64_t* hist_state,
+                  uint64_t* hist_draws);
+
 double or_norm_cdf(double z);
 double or_norm_ppf(double p);
 int or_shapiro_wilk(const double* x, int n, double* w, double* p);

@@ -183,3 +183,36 @@ def to_mc_box(b, mc):
                          stride_q=b["stride_q"], id_offset=b["id_offset"], key=b["key"],
                          tally_offset=b["tally_offset"], box=ctypes.pointer(spec))
     return prob, spec
+
+
+# --- the paper's Section 5 problem (AZURV1-like, supercritical) -----------------
+#   azurv1  infinite homogeneous medium, Sigma_t = 1, speed 1, pulse at
+#           t = x = 0, scattering ratio 0.4 with multiplicity 2.75 (k = 1.1),
+#           census at t = 20; collision-estimator flux averaged over
+#           x in [-1, 1] in 20 unit time bins; 30 repetitions x 1000 batches x
+#           1000 source particles
+
+def azurv1(seeding=SEED_HASH_HIER, n_reps=30, n_batches=1000, per_batch=1000, c=0.4, nu=2.75, t_end=20.0,
+           x_half=1.0, n_time_bins=20, tally_offset=0, seed=None):
+    if seed is None:
+        seed = STRIDE_X0 if seeding == SEED_STRIDE else HASH_SEED
+    return dict(c=float(c), nu=float(nu), t_end=float(t_end), x_half=float(x_half), sigma_t=1.0,
+                seed=int(seed), stride_q=STRIDE_Q, id_offset=0, tally_offset=int(tally_offset),
+                n_reps=int(n_reps), n_batches=int(n_batches), per_batch=int(per_batch),
+                n_time_bins=int(n_time_bins), seeding=int(seeding))
+
+
+def azurv1_histories(a):
+    return a["n_reps"] * a["n_batches"] * a["per_batch"]
+
+
+def azurv1_tally_slots(a):
+    return a["tally_offset"] + a["n_reps"] * a["n_batches"] * a["n_time_bins"]
+
+
+def to_oracle_azurv1(a, oracle):
+    return oracle.Azurv1Problem(c=a["c"], nu=a["nu"], t_end=a["t_end"], x_half=a["x_half"],
+                                sigma_t=a["sigma_t"], seed=a["seed"], stride_q=a["stride_q"],
+                                id_offset=a["id_offset"], tally_offset=a["tally_offset"],
+                                n_reps=a["n_reps"], n_batches=a["n_batches"], per_batch=a["per_batch"],
+                                n_time_bins=a["n_time_bins"], seeding=a["seeding"], pad=0)
