@@ -137,7 +137,7 @@ MC_API int mc_lcg_draw(mc_ctx* ctx, const mc_lcg* lcg, const mc_seed_spec* seed,
  * scheduling and bit-identical across launch shapes and schedules. */
 enum { MC_SEED_HASH = 0, MC_SEED_STRIDE = 1, MC_SEED_HASH_HIER = 2 };
 enum { MC_SRC_ISOTROPIC = 0, MC_SRC_BEAM = 1 };
-enum { MC_GEOM_SLAB = 0, MC_GEOM_BOX = 1 };
+enum { MC_GEOM_SLAB = 0, MC_GEOM_BOX = 1, MC_GEOM_PULSE = 2 };
 enum { MC_FP64 = 0, MC_FP32_GUARDED = 1 };
 enum { MC_SCHED_HISTORY = 0, MC_SCHED_EVENT = 1, MC_SCHED_AUTO = 2 };
 
@@ -156,8 +156,24 @@ typedef struct {
     uint32_t reserved;
 } mc_box_spec;
 
+/* Pulse problem data (geometry MC_GEOM_PULSE; Section 5's supercritical,
+ * time-dependent test): a pulse at t = x = 0 in an infinite homogeneous
+ * medium (speed 1), collisions scatter with probability c into
+ * floor(nu + u) outgoing particles (k = c * nu), census at t_end; the
+ * collision-estimator flux over [-x_half, x_half] is tallied in unit time
+ * bins [j, j+1), j < n_time_bins, per (repetition, batch).  Secondaries get
+ * hash seeds S_c = hash(k, S_p) (Eq. 5) unless seeding is MC_SEED_STRIDE, in
+ * which case a history's secondaries draw from its one stream, depth-first.
+ * Histories: n_reps * n_batches * per_batch; history g belongs to rep
+ * g / (n_batches * per_batch) and batch (g / per_batch) % n_batches;
+ * MC_SEED_HASH_HIER seeds it with hash(particle, hash(batch, hash(rep, s))). */
 typedef struct {
-    uint32_t geometry;    /* MC_GEOM_SLAB or MC_GEOM_BOX                           */
+    double c, nu, t_end, x_half, sigma_t;
+    uint32_t n_reps, n_batches, per_batch, n_time_bins;
+} mc_pulse_spec;
+
+typedef struct {
+    uint32_t geometry;    /* MC_GEOM_SLAB, MC_GEOM_BOX or MC_GEOM_PULSE            */
     uint32_t source;      /* MC_SRC_ISOTROPIC (uniform in the slab/box) or BEAM   */
     uint32_t seeding;     /* MC_SEED_HASH, MC_SEED_STRIDE, MC_SEED_HASH_HIER       */
     uint32_t n_bins;      /* slab: equal-width bins over [0,L]; box: mesh^3        */
@@ -173,6 +189,8 @@ typedef struct {
     uint64_t key;         /* hierarchical hash key i                               */
     uint64_t tally_offset;/* first int64 slot of this problem: [batch][bin]        */
     const mc_box_spec* box; /* geometry MC_GEOM_BOX only                           */
+    const mc_pulse_spec* pulse; /* geometry MC_GEOM_PULSE only: n_bins = n_time_bins, */
+                            /* n_batches = n_reps * n_batches (one call, one problem) */
 } mc_problem;
 
 typedef struct {
@@ -196,7 +214,8 @@ enum {
     MC_C_SOURCE = 0, MC_C_FLIGHTS, MC_C_COLLISIONS, MC_C_ABSORPTIONS, MC_C_SCATTERS,
     MC_C_LEAK_LO, MC_C_LEAK_HI, MC_C_DRAWS, MC_C_EXCEED_HIST, MC_C_EXCEED_DRAWS,
     MC_C_SPLITS, MC_C_ROULETTE_KILLS, MC_C_CAPPED, MC_C_MAX_DRAWS, MC_C_CHILDREN,
-    MC_C_RESERVED, MC_NCOUNT
+    MC_C_DROPPED, /* secondaries lost to a full bounded stack (MC_ERR_CAPACITY) */
+    MC_NCOUNT
 };
 
 typedef struct {

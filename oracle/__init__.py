@@ -26,7 +26,7 @@ NCOUNT = 16
 COUNT_NAMES = [
     "source", "flights", "collisions", "absorptions", "scatters", "leak_lo", "leak_hi",
     "draws", "exceed_hist", "exceed_draws", "splits", "roulette_kills", "capped",
-    "max_draws", "children", "reserved",
+    "max_draws", "children", "dropped",
 ]
 SEED_HASH, SEED_STRIDE, SEED_HASH_HIER = 0, 1, 2
 SRC_ISOTROPIC, SRC_BEAM = 0, 1

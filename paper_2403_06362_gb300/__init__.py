@@ -19,7 +19,8 @@ import numpy as np
 
 from . import _ffi
 from ._ffi import (  # noqa: F401  (re-exported names)
-    COUNT_NAMES, MC_FP32_GUARDED, MC_FP64, MC_GEOM_BOX, MC_GEOM_SLAB, MC_NCOUNT, MC_SCHED_AUTO,
+    COUNT_NAMES, MC_FP32_GUARDED, MC_FP64, MC_GEOM_BOX, MC_GEOM_PULSE, MC_GEOM_SLAB, MC_NCOUNT,
+    MC_SCHED_AUTO, mc_pulse_spec,
     MC_SCHED_EVENT, MC_SCHED_HISTORY, MC_SEED_HASH, MC_SEED_HASH_HIER, MC_SEED_STRIDE,
     MC_SRC_BEAM, MC_SRC_ISOTROPIC, McError, mc_box_spec, mc_lcg, mc_problem, mc_run_config,
     mc_seed_spec, mc_tally,

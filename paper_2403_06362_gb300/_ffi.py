@@ -18,7 +18,7 @@ MC_OK, MC_ERR_ARG, MC_ERR_CUDA, MC_ERR_OVERFLOW = 0, -1, -2, -3
 MC_ERR_EVENT_CAP, MC_ERR_TIMEOUT, MC_ERR_CAPACITY, MC_ERR_STATE = -4, -5, -6, -7
 MC_SEED_HASH, MC_SEED_STRIDE, MC_SEED_HASH_HIER = 0, 1, 2
 MC_SRC_ISOTROPIC, MC_SRC_BEAM = 0, 1
-MC_GEOM_SLAB, MC_GEOM_BOX = 0, 1
+MC_GEOM_SLAB, MC_GEOM_BOX, MC_GEOM_PULSE = 0, 1, 2
 MC_FP64, MC_FP32_GUARDED = 0, 1
 MC_SCHED_HISTORY, MC_SCHED_EVENT, MC_SCHED_AUTO = 0, 1, 2
 MC_NCOUNT = 16
@@ -26,7 +26,7 @@ MC_BOX_MAX_GROUPS = 8
 COUNT_NAMES = [
     "source", "flights", "collisions", "absorptions", "scatters", "leak_lo", "leak_hi",
     "draws", "exceed_hist", "exceed_draws", "splits", "roulette_kills", "capped",
-    "max_draws", "children", "reserved",
+    "max_draws", "children", "dropped",
 ]
 
 EXPORTED = [
@@ -65,6 +65,14 @@ class mc_box_spec(C.Structure):
     ]
 
 
+class mc_pulse_spec(C.Structure):
+    _fields_ = [
+        ("c", C.c_double), ("nu", C.c_double), ("t_end", C.c_double), ("x_half", C.c_double),
+        ("sigma_t", C.c_double), ("n_reps", C.c_uint32), ("n_batches", C.c_uint32),
+        ("per_batch", C.c_uint32), ("n_time_bins", C.c_uint32),
+    ]
+
+
 class mc_problem(C.Structure):
     _fields_ = [
         ("geometry", C.c_uint32), ("source", C.c_uint32), ("seeding", C.c_uint32),
@@ -72,7 +80,7 @@ class mc_problem(C.Structure):
         ("L", C.c_double), ("sigma_t", C.c_double), ("c", C.c_double),
         ("n_histories", C.c_uint64), ("seed", C.c_uint64), ("stride_q", C.c_uint64),
         ("id_offset", C.c_uint64), ("key", C.c_uint64), ("tally_offset", C.c_uint64),
-        ("box", C.POINTER(mc_box_spec)),
+        ("box", C.POINTER(mc_box_spec)), ("pulse", C.POINTER(mc_pulse_spec)),
     ]
 
 

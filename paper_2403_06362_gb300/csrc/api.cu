@@ -86,6 +86,10 @@ constexpr size_t kScratchBytes = 256;
 int stage_host(mc_ctx* ctx, const mc_problem* problems, uint32_t n, size_t* bytes_out) {
   const bool box = problems[0].geometry == MC_GEOM_BOX;
   const size_t bytes = (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
+  if (problems[0].geometry == MC_GEOM_PULSE) {
+    mci::set_error("graph replay covers the slab history schedule only");
+    return MC_ERR_ARG;
+  }
   if (ctx->staged) MC_TRY_CUDA(cudaEventSynchronize(ctx->staged));
   if (bytes > ctx->h_problems_bytes) {
     if (ctx->h_problems) cudaFreeHost(ctx->h_problems);
@@ -105,7 +109,9 @@ int stage_host(mc_ctx* ctx, const mc_problem* problems, uint32_t n, size_t* byte
 
 int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStream_t s) {
   const bool box = problems[0].geometry == MC_GEOM_BOX;
-  const size_t bytes = (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
+  const bool pulse = problems[0].geometry == MC_GEOM_PULSE;
+  const size_t bytes = pulse ? mci::pulse_dev_size()
+                             : (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
   cudaEvent_t* ev = &ctx->staged;
   if (*ev) MC_TRY_CUDA(cudaEventSynchronize(*ev));
   if (bytes > ctx->h_problems_bytes) {
@@ -117,11 +123,13 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
   }
   int st = ctx->problems.reserve(bytes);
   if (st != MC_OK) return st;
-  if (box) mci::box_fill_host(problems, n, ctx->h_problems);
+  if (pulse) mci::pulse_fill_host(problems, ctx->h_problems);
+  else if (box) mci::box_fill_host(problems, n, ctx->h_problems);
   else mci::slab_fill_host(problems, n, ctx->h_problems);
   MC_TRY_CUDA(cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, s));
   if (!*ev) MC_TRY_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   MC_TRY_CUDA(cudaEventRecord(*ev, s));
+  if (pulse) return mci::pulse_prep(ctx->problems.ptr, s);
   return box ? mci::box_prep(ctx->problems.ptr, n, s) : mci::slab_prep(ctx->problems.ptr, n, s);
 }
 
@@ -152,9 +160,31 @@ int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t*
   uint64_t acc = 0;
   for (uint32_t i = 0; i < n; ++i) {
     const mc_problem& q = p[i];
-    if (q.geometry != p[0].geometry || q.geometry > MC_GEOM_BOX) {
-      mci::set_error("problem %u: all problems of one call must share one geometry (slab or box)", i);
+    if (q.geometry != p[0].geometry || q.geometry > MC_GEOM_PULSE) {
+      mci::set_error("problem %u: all problems of one call must share one geometry (slab, box or pulse)", i);
       return MC_ERR_ARG;
+    }
+    if (q.geometry == MC_GEOM_PULSE) {
+      const mc_pulse_spec* ps = q.pulse;
+      const bool ok = n == 1 && ps && ps->sigma_t > 0.0 && std::isfinite(ps->sigma_t) && ps->c >= 0.0 &&
+                      ps->c <= 1.0 && ps->nu >= 1.0 && ps->nu <= 64.0 && ps->t_end > 0.0 &&
+                      ps->t_end <= 1.0e6 && ps->x_half >= 0.0 && ps->n_reps >= 1 && ps->n_batches >= 1 &&
+                      ps->per_batch >= 1 && ps->n_time_bins >= 1 && q.n_bins == ps->n_time_bins &&
+                      (uint64_t)q.n_batches == (uint64_t)ps->n_reps * ps->n_batches &&
+                      q.n_histories == (uint64_t)ps->n_reps * ps->n_batches * ps->per_batch &&
+                      q.seeding <= MC_SEED_HASH_HIER && q.reserved == 0;
+      if (!ok) {
+        mci::set_error("problem %u: invalid pulse problem (one problem per call; spec, n_bins = n_time_bins, "
+                       "n_batches = reps * batches, n_histories = reps * batches * per_batch)", i);
+        return MC_ERR_ARG;
+      }
+      const uint64_t slots = (uint64_t)q.n_bins * q.n_batches;
+      if (q.tally_offset > t->n_slots || slots > t->n_slots - q.tally_offset) {
+        mci::set_error("problem %u: pulse tally slots outside the tally", i);
+        return MC_ERR_ARG;
+      }
+      acc += q.n_histories;
+      continue;
     }
     if (q.geometry == MC_GEOM_BOX) {
       int st = check_box(q, i);
@@ -445,6 +475,20 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
   if (re == rb) return MC_OK;
 
   if (problems[0].geometry == MC_GEOM_BOX) return run_box(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, s);
+  if (problems[0].geometry == MC_GEOM_PULSE) {
+    mci::PulseLaunch P{};
+    P.d_prob = ctx->problems.ptr;
+    P.range_begin = rb;
+    P.total = re - rb;
+    P.chunk = cfg->chunk ? cfg->chunk : 32u;
+    P.d_ticket = ticket;
+    P.tally = tally;
+    P.lcg = *lcg;
+    P.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 24);
+    P.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 128;
+    P.num_sms = ctx->num_sms;
+    return mci::pulse_run(P, s);
+  }
 
   mci::SlabLaunch L{};
   st = make_slab_launch(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, &L);
@@ -629,6 +673,7 @@ MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t probl
     const double h = p.box->side / (double)p.box->mesh;
     vol = h * h * h;
   }
+  if (p.geometry == MC_GEOM_PULSE && p.pulse) vol = 2.0 * p.pulse->x_half;  // unit time bins
   const double scale = std::ldexp(1.0, -32);
   const uint64_t N = p.n_histories;
   bool overflow = false;
@@ -669,6 +714,11 @@ MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t probl
   if (overflow) {
     mci::set_error("mc_tally_read: a bin of problem %u reached the int64 headroom 2^62", problem);
     return MC_ERR_OVERFLOW;
+  }
+  if (cnt[MC_C_DROPPED] != 0) {
+    mci::set_error("mc_tally_read: %llu secondaries of problem %u were dropped (full stack)",
+                   (unsigned long long)cnt[MC_C_DROPPED], problem);
+    return MC_ERR_CAPACITY;
   }
   if (cnt[MC_C_CAPPED] != 0) {
     mci::set_error("mc_tally_read: %llu histories of problem %u hit the event cap",

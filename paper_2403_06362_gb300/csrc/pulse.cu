@@ -1,0 +1,291 @@
+// pulse.cu -- the supercritical, time-dependent pulse problem of Section 5:
+// a pulse at t = x = 0 in an infinite homogeneous medium, scattering with
+// multiplicity (k = c * nu > 1), census at t_end, and the collision-estimator
+// flux averaged over [-x_half, x_half] in unit time bins, tallied per
+// (repetition, batch).
+//
+// History-based: a lane follows one source particle and its whole family of
+// secondaries depth-first.  Secondaries wait on a per-lane last-in first-out
+// stack (thread-local memory).  In hash mode each secondary owns a stream
+// seeded on demand by S_c = hash(k, S_p) (Section 4, Eq. 5), so no lane ever
+// coordinates with another; in stride mode the family shares the source
+// particle's stream, which fixes the depth-first order the secondaries are
+// drawn in -- the sequential bookkeeping the paper's hashing removes.
+// The fp64 arithmetic is rounded once per operation (--fmad=false).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "internal.h"
+#include "slab.cuh"
+#include "transport.h"
+
+namespace {
+
+struct PulseDev {
+  double c, nu, t_end, x_half, sigma_t;
+  uint64_t n_hist, seed, stride_q, id_offset, tally_offset;
+  uint32_t n_reps, n_batches, per_batch, n_time_bins, seeding, pad;
+  // derived by pulse_prep_kernel
+  double inv_st;
+  long long unit;      // llrint(2^32 / Sigma_t): one collision-estimator score
+  uint64_t seed_hash;  // flat hash mode: seed half of hash(., s)
+};
+
+constexpr int kStack = 256;
+
+struct Pending {
+  double x, t;
+  uint64_t seed;
+};
+
+struct PulseArgs {
+  const PulseDev* prob;
+  uint64_t range_begin, total;
+  uint32_t chunk;
+  unsigned long long* ticket;
+  unsigned long long* tally;
+  unsigned long long* counts;
+  uint64_t* hist_state;
+  uint64_t* hist_draws;
+  mcd::Lcg lcg;
+  uint64_t event_cap;
+};
+
+__global__ void pulse_prep_kernel(PulseDev* p) {
+  if (threadIdx.x == 0) {
+    p->inv_st = 1.0 / p->sigma_t;
+    p->unit = __double2ll_rn(p->inv_st * mcs::kFix);
+    p->seed_hash = mcd::seed_hash_of(p->seed);
+  }
+}
+
+__device__ __forceinline__ uint64_t pulse_seed(const PulseDev& P, uint64_t g, const mcd::Affine* tab,
+                                               uint64_t mask) {
+  if (P.seeding == MC_SEED_STRIDE) return mcs::skip_tab(tab, P.seed, P.stride_q * (P.id_offset + g)) & mask;
+  if (P.seeding == MC_SEED_HASH) return mcd::hash_with(g, P.seed_hash) & mask;
+  const uint64_t pb = P.per_batch, nb = P.n_batches;
+  const uint64_t rep = g / (pb * nb), batch = (g / pb) % nb, part = g % pb;
+  const uint64_t h_rep = mcd::hash64(rep, P.seed);
+  return mcd::hash64(part, mcd::hash64(batch, h_rep)) & mask;
+}
+
+struct PulseCounts {
+  uint64_t src, flights, coll, absn, scat, census, children, capped, dropped, draws, exh, exd, maxd;
+  __device__ void flush(unsigned long long* c) {
+    if (src) atomicAdd(c + MC_C_SOURCE, (unsigned long long)src);
+    if (flights) atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)flights);
+    if (coll) atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)coll);
+    if (absn) atomicAdd(c + MC_C_ABSORPTIONS, (unsigned long long)absn);
+    if (scat) atomicAdd(c + MC_C_SCATTERS, (unsigned long long)scat);
+    if (census) atomicAdd(c + MC_C_LEAK_HI, (unsigned long long)census);
+    if (children) atomicAdd(c + MC_C_CHILDREN, (unsigned long long)children);
+    if (capped) atomicAdd(c + MC_C_CAPPED, (unsigned long long)capped);
+    if (dropped) atomicAdd(c + MC_C_DROPPED, (unsigned long long)dropped);
+    if (draws) atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
+    if (exh) atomicAdd(c + MC_C_EXCEED_HIST, (unsigned long long)exh);
+    if (exd) atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)exd);
+    if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
+  }
+};
+
+template <int M>
+__global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
+  __shared__ mcd::Affine tab[64];
+  __shared__ PulseDev sP;
+  if (threadIdx.x == 0) {
+    mcd::Affine sq{a.lcg.g, a.lcg.c};
+    for (int j = 0; j < 64; ++j) { tab[j] = sq; sq = mcd::compose(sq, sq); }
+    sP = *a.prob;
+  }
+  __syncthreads();
+  const PulseDev& P = sP;
+  const mcd::Lcg l = a.lcg;
+  const bool hash_mode = P.seeding != MC_SEED_STRIDE;
+  const unsigned kFull = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  Pending stack[kStack];
+  uint32_t sp = 0;
+  uint64_t pool_next = 0, pool_end = 0;
+  bool more = true, alive = false, primary = false;
+  PulseCounts lc{};
+  mcs::Rng<M> r{0ull, 0ull};
+  double x = 0.0, t = 0.0, mu = 0.0;
+  uint64_t gi = 0, events = 0, fam_draws = 0;
+  unsigned long long* row = nullptr;
+
+  for (;;) {
+    unsigned dead = __ballot_sync(kFull, !alive);
+    while (dead != 0u && more) {
+      if (pool_next >= pool_end) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.ticket, (unsigned long long)a.chunk);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (b0 >= a.total) { more = false; break; }
+        pool_next = b0;
+        pool_end = min((uint64_t)b0 + (uint64_t)a.chunk, (uint64_t)a.total);
+      }
+      const uint64_t avail = pool_end - pool_next;
+      const unsigned rank = __popc(dead & lt_mask);
+      if (!alive && rank < avail) {
+        gi = a.range_begin + pool_next + rank;
+        row = a.tally + P.tally_offset + (gi / P.per_batch) * P.n_time_bins;
+        r = mcs::Rng<M>{pulse_seed(P, gi, tab, l.mask), 0ull};
+        x = 0.0;
+        t = 0.0;
+        mu = 2.0 * r.next(l) - 1.0;
+        events = 0;
+        fam_draws = 0;
+        sp = 0;
+        primary = true;
+        ++lc.src;
+        alive = true;
+      }
+      pool_next += min((uint64_t)__popc(dead), avail);
+      dead = __ballot_sync(kFull, !alive);
+    }
+    if (__ballot_sync(kFull, alive) == 0u) break;
+    if (!alive) continue;
+
+    bool ended = false;
+    if (events == a.event_cap) {
+      ++lc.capped;
+      ended = true;
+    } else {
+      ++events;
+      ++lc.flights;
+      const double d = -log(1.0 - r.next(l)) * P.inv_st;
+      const double tn = t + d;
+      if (tn >= P.t_end) {
+        ++lc.census;
+        ended = true;
+      } else {
+        const double xn = x + d * mu;
+        ++lc.coll;
+        if (xn >= -P.x_half && xn <= P.x_half) {
+          uint32_t j = (uint32_t)floor(tn);
+          if (j >= P.n_time_bins) j = P.n_time_bins - 1;
+          atomicAdd(row + j, (unsigned long long)P.unit);
+        }
+        x = xn;
+        t = tn;
+        if (r.next(l) < P.c) {
+          ++lc.scat;
+          const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
+          for (uint32_t k = 0; k + 1 < n; ++k) {
+            if (sp < (uint32_t)kStack) {
+              stack[sp].x = x;
+              stack[sp].t = t;
+              stack[sp].seed = hash_mode ? (mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask) : 0ull;
+              ++sp;
+              ++lc.children;
+            } else {
+              ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
+            }
+          }
+          mu = 2.0 * r.next(l) - 1.0;
+        } else {
+          ++lc.absn;
+          ended = true;
+        }
+      }
+    }
+    if (!ended) continue;
+    // the current particle ended
+    if (hash_mode) {
+      fam_draws += r.draws;
+      if (r.draws > lc.maxd) lc.maxd = r.draws;
+      if (primary) {
+        if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
+        if (a.hist_draws) a.hist_draws[gi] = r.draws;
+        if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
+      }
+    }
+    primary = false;
+    events = 0;
+    if (sp > 0) {
+      --sp;
+      x = stack[sp].x;
+      t = stack[sp].t;
+      if (hash_mode) r = mcs::Rng<M>{stack[sp].seed, 0ull};
+      mu = 2.0 * r.next(l) - 1.0;
+      continue;
+    }
+    if (!hash_mode) {
+      fam_draws = r.draws;
+      if (r.draws > lc.maxd) lc.maxd = r.draws;
+      if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
+      if (a.hist_draws) a.hist_draws[gi] = r.draws;
+      if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
+    }
+    lc.draws += fam_draws;
+    alive = false;
+  }
+  lc.flush(a.counts);
+}
+
+}  // namespace
+
+namespace mci {
+
+size_t pulse_dev_size() { return sizeof(PulseDev); }
+
+int pulse_fill_host(const mc_problem* src, void* dst) {
+  PulseDev q;
+  std::memset(&q, 0, sizeof q);
+  const mc_pulse_spec* s = src->pulse;
+  q.c = s->c;
+  q.nu = s->nu;
+  q.t_end = s->t_end;
+  q.x_half = s->x_half;
+  q.sigma_t = s->sigma_t;
+  q.n_hist = src->n_histories;
+  q.seed = src->seed;
+  q.stride_q = src->stride_q;
+  q.id_offset = src->id_offset;
+  q.tally_offset = src->tally_offset;
+  q.n_reps = s->n_reps;
+  q.n_batches = s->n_batches;
+  q.per_batch = s->per_batch;
+  q.n_time_bins = s->n_time_bins;
+  q.seeding = src->seeding;
+  std::memcpy(dst, &q, sizeof q);
+  return MC_OK;
+}
+
+int pulse_prep(void* d_prob, cudaStream_t s) {
+  pulse_prep_kernel<<<1, 32, 0, s>>>(static_cast<PulseDev*>(d_prob));
+  return cuda_status(cudaGetLastError(), "pulse_prep_kernel launch");
+}
+
+int pulse_run(const PulseLaunch& L, cudaStream_t s) {
+  PulseArgs a{};
+  a.prob = static_cast<const PulseDev*>(L.d_prob);
+  a.range_begin = L.range_begin;
+  a.total = L.total;
+  a.chunk = L.chunk;
+  a.ticket = L.d_ticket;
+  a.tally = reinterpret_cast<unsigned long long*>(L.tally->d_bins);
+  a.counts = reinterpret_cast<unsigned long long*>(L.tally->d_counts);
+  a.hist_state = L.tally->d_hist_state;
+  a.hist_draws = L.tally->d_hist_draws;
+  a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
+  a.event_cap = L.event_cap;
+  auto k = L.lcg.m == 63 ? pulse_kernel<63> : pulse_kernel<0>;
+  int per_sm = 0;
+  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
+                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");
+  if (st != MC_OK) return st;
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t warps_needed = (a.total + a.chunk - 1) / a.chunk;
+  const uint64_t blocks_needed = (warps_needed * 32 + L.block - 1) / L.block;
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)L.num_sms * per_sm, blocks_needed));
+  k<<<grid, L.block, 0, s>>>(a);
+  return cuda_status(cudaGetLastError(), "pulse_kernel launch");
+}
+
+}  // namespace mci

@@ -65,6 +65,23 @@ struct BoxLaunch {
   cudaStream_t capture_stream;
 };
 
+// One run of the pulse problem (pulse.cu).
+struct PulseLaunch {
+  const void* d_prob;
+  uint64_t range_begin, total;
+  uint32_t chunk;
+  unsigned long long* d_ticket;
+  const mc_tally* tally;
+  mc_lcg lcg;
+  uint64_t event_cap;
+  int block, num_sms;
+};
+
+size_t pulse_dev_size();
+int pulse_fill_host(const mc_problem* src, void* dst);
+int pulse_prep(void* d_prob, cudaStream_t s);
+int pulse_run(const PulseLaunch& L, cudaStream_t s);
+
 size_t box_dev_size();
 size_t box_child_rec_size();
 int box_fill_host(const mc_problem* src, uint32_t n, void* dst);

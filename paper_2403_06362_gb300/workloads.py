@@ -216,3 +216,18 @@ def to_oracle_azurv1(a, oracle):
                                 id_offset=a["id_offset"], tally_offset=a["tally_offset"],
                                 n_reps=a["n_reps"], n_batches=a["n_batches"], per_batch=a["per_batch"],
                                 n_time_bins=a["n_time_bins"], seeding=a["seeding"], pad=0)
+
+
+def to_mc_pulse(a, mc):
+    """dict -> (libmc mc_problem, mc_pulse_spec); keep the spec alive while
+    the problem is in use."""
+    import ctypes
+    spec = mc.mc_pulse_spec(c=a["c"], nu=a["nu"], t_end=a["t_end"], x_half=a["x_half"], sigma_t=a["sigma_t"],
+                            n_reps=a["n_reps"], n_batches=a["n_batches"], per_batch=a["per_batch"],
+                            n_time_bins=a["n_time_bins"])
+    prob = mc.mc_problem(geometry=mc.MC_GEOM_PULSE, source=0, seeding=a["seeding"], n_bins=a["n_time_bins"],
+                         n_batches=a["n_reps"] * a["n_batches"], reserved=0, L=0.0, sigma_t=a["sigma_t"],
+                         c=a["c"], n_histories=azurv1_histories(a), seed=a["seed"], stride_q=a["stride_q"],
+                         id_offset=a["id_offset"], key=0, tally_offset=a["tally_offset"], box=None,
+                         pulse=ctypes.pointer(spec))
+    return prob, spec
