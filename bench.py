@@ -519,6 +519,36 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                            "histories_per_s_batched_fp32": nh / (best32 / 1e3),
                            "speedup_batched_fp32_over_single_fp64": ms_single / best32}
 
+    # Section 5 experiment: 30 repetitions x 1000 batches x 1000 sources, hash
+    # (hierarchical seeds) vs stride; Shapiro-Wilk on each of the 20 points
+    # over the 1000 batch means, per repetition (600 tests per mode)
+    for sname, sd in (("hash", W.SEED_HASH_HIER), ("stride", W.SEED_STRIDE)):
+        a = W.azurv1(seeding=sd)
+        prob, spec = W.to_mc_pulse(a, mc)
+        cp = mc.problem_array([prob])
+        tally = mc.Tally(W.azurv1_tally_slots(a), 1)
+        cfg = mc.mc_run_config()
+        mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream)
+        flux = r.batch.reshape(a["n_reps"], a["n_batches"], a["n_time_bins"])
+        pvals = np.array([mc.mc_normality(flux[k])[2] for k in range(a["n_reps"])])  # [rep][point]
+        n = W.azurv1_histories(a)
+        res[f"pulse_paper_{sname}"] = {
+            "ms": ms, "source_histories_per_s": n / (ms / 1e3), "collisions_per_s": r.counts["collisions"] / (ms / 1e3),
+            "census_per_source": r.counts["leak_hi"] / n, "secondaries": r.counts["children"],
+            "sw_fails_p_lt_0.05": int(np.sum(pvals < 0.05)), "sw_tests": int(pvals.size),
+            "sw_median_p_per_point": [float(v) for v in np.median(pvals, axis=0)],
+            "paper_fails_context": {"hash": "339/600", "stride": "369/600"}[sname],
+            "paper_runtime_context": {"hash": "111.46 s (serial Python)", "stride": "113.26 s (serial Python)"}[sname]}
+        del spec
+
     # 3D two-region box, 10^8 source histories
     box = W.box_large(W.SEED_HASH)
     n = box["n_histories"]

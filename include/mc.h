@@ -241,9 +241,10 @@ MC_API int mc_transport_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* pr
 /* Launch-shape autotuner for mc_transport_run (schedule MC_SCHED_AUTO calls
  * it on the first run of each workload shape and caches the answer in the
  * context).  Times every candidate -- history schedule with block 128/256/512
- * and three chunk sizes, and the event schedule as a captured graph -- on a
- * sample of the histories (all of them up to 2^16, else max(2^16, 1/8) from
- * the middle of the list), writing only into a context-owned scratch tally;
+ * and chunks of 1/4, 1 and 4 times the default, and the event schedule as a
+ * captured graph -- on a sample of the histories (all of them up to 2^17,
+ * else max(2^17, 1/4) from the middle of the list), writing only into a
+ * context-owned scratch tally;
  * the caller's tally is not touched.  *best receives `base` with schedule,
  * block, chunk and use_graph replaced by the fastest candidate; *best_ms
  * (nullable) its time on the sample.  Results never depend on the choice:

@@ -368,9 +368,9 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const 
   L.n_problems = n_problems;
   // Default chunk: about four grabs per resident warp (fine-grained enough to
   // balance long-tailed histories, coarse enough that lanes rarely change
-  // problem in a batched launch), within [32, 256].
+  // problem in a batched launch), within [32, 1024].
   L.chunk = cfg->chunk ? cfg->chunk
-                       : (uint32_t)std::min<uint64_t>(256, std::max<uint64_t>(32, (re - rb) / ((uint64_t)ctx->num_sms * 256)));
+                       : (uint32_t)std::min<uint64_t>(1024, std::max<uint64_t>(32, (re - rb) / ((uint64_t)ctx->num_sms * 256)));
   L.range_begin = rb;
   L.total = re - rb;
   L.d_ticket = ticket;
@@ -544,15 +544,19 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
   t2.d_bins = static_cast<int64_t*>(ctx->tune_tally.ptr);
   t2.n_slots = tally->n_slots;
   t2.d_counts = reinterpret_cast<uint64_t*>(static_cast<char*>(ctx->tune_tally.ptr) + bins);
-  // A sample from the middle of the concatenated history list.
-  const uint64_t S = total <= (1ull << 16) ? total : std::max<uint64_t>(1ull << 16, total / 8);
+  // A sample from the middle of the concatenated history list: all of it up
+  // to 2^17 histories, else a quarter (at least 2^17).
+  const uint64_t S = total <= (1ull << 17) ? total : std::max<uint64_t>(1ull << 17, total / 4);
   const uint64_t start = (total - S) / 2;
   struct Cand { uint32_t schedule, block, chunk, graph; };
   const bool box = problems[0].geometry == MC_GEOM_BOX;
+  // Chunks relative to the default for the full run (histories per warp
+  // grab; see transport_run_impl), so the sample ranks them as the run would.
+  const uint64_t c0 = std::min<uint64_t>(1024, std::max<uint64_t>(32, total / ((uint64_t)ctx->num_sms * 256)));
   std::vector<Cand> cands;
   for (uint32_t b : box ? std::vector<uint32_t>{128u, 256u} : std::vector<uint32_t>{128u, 256u, 512u})
-    for (uint32_t c : {8u, 32u, 128u})
-      cands.push_back({MC_SCHED_HISTORY, b, c, 0u});
+    for (uint64_t c : {c0 / 4, c0, c0 * 4})
+      cands.push_back({MC_SCHED_HISTORY, b, (uint32_t)std::max<uint64_t>(8, c), 0u});
   cands.push_back({MC_SCHED_EVENT, 256u, 0u, 1u});
   cudaEvent_t e0, e1;
   MC_TRY_CUDA(cudaEventCreate(&e0));
