@@ -111,3 +111,22 @@ def test_box_auto_schedule_matches(env):
     auto = gpu_box(env, b, hist=False, schedule=2)
     assert np.array_equal(ref.bins.cpu().numpy(), auto.bins.cpu().numpy())
     assert np.array_equal(counts_of(ref), counts_of(auto))
+
+
+def test_box_full_size_sampled(env, oracle):
+    """10^8 source histories (the benchmark's box) in the default launch
+    shape, fp64; 200 sampled histories rerun one by one by the oracle must
+    match in the primary's final state and draw count."""
+    b = W.box_large(W.SEED_HASH)
+    t = gpu_box(env, b)
+    hs = t.hist_state.cpu().numpy().view(np.uint64)
+    hd = t.hist_draws.cpu().numpy().view(np.uint64)
+    L = oracle.Lcg(m=63, pad=0, g=W.LCG_G, c=1)
+    P = W.to_oracle_box(b, oracle)
+    rng = np.random.default_rng(5)
+    for i in np.unique(rng.integers(0, b["n_histories"], 200)):
+        r = oracle.box_run(L, P, int(i), int(i) + 1, per_history=True)
+        assert int(r["hist_state"][0]) == int(hs[i]) and int(r["hist_draws"][0]) == int(hd[i]), i
+    c = counts_of(t)
+    assert int(c[0]) == b["n_histories"] and int(c[12]) == 0
+    assert int(c[0]) + int(c[14]) == int(c[6]) + int(c[11])

@@ -267,3 +267,23 @@ def test_tally_overflow_reported(env):
     tally.bins[7] = 2**62  # a bin at the headroom limit
     r = mc.mc_tally_read(ctx, cprobs, 0, tally.c, check=False)
     assert r.status == mc._ffi.MC_ERR_OVERFLOW
+
+
+def test_batched_full_size_sampled(env, oracle):
+    """All 256 batched problems at full size (~4e7 histories, one launch,
+    fp64, default shape); 300 sampled histories rerun by the oracle."""
+    probs = W.slab_batched(W.SEED_HASH_HIER)
+    tally, _ = gpu_run(env, probs)
+    hs = tally.hist_state.cpu().numpy().view(np.uint64)
+    hd = tally.hist_draws.cpu().numpy().view(np.uint64)
+    starts = np.cumsum([0] + [p["n_histories"] for p in probs])
+    rng = np.random.default_rng(11)
+    for g in np.unique(rng.integers(0, starts[-1], 300)):
+        k = int(np.searchsorted(starts, g, side="right") - 1)
+        P = W.to_oracle_problem(probs[k], oracle)
+        i = int(g - starts[k])
+        r = oracle.slab_run(olcg(oracle), P, i, i + 1, per_history=True)
+        assert int(r["hist_state"][0]) == int(hs[g]) and int(r["hist_draws"][0]) == int(hd[g]), g
+    c = counts_of(tally, len(probs))
+    assert np.array_equal(c[:, 0], np.array([p["n_histories"] for p in probs], dtype=np.uint64))
+    assert np.array_equal(c[:, 0], c[:, 3] + c[:, 5] + c[:, 6])
