@@ -360,10 +360,11 @@ int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uin
   return MC_OK;
 }
 
-int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_config* cfg,
-                     const mc_tally* tally, uint64_t rb, uint64_t re, unsigned long long* ticket,
-                     mci::SlabLaunch* out) {
+int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
+                     const mc_run_config* cfg, const mc_tally* tally, uint64_t rb, uint64_t re,
+                     unsigned long long* ticket, mci::SlabLaunch* out) {
   mci::SlabLaunch L{};
+  L.single_n_bins = n_problems == 1 ? problems[0].n_bins : 0u;
   L.d_probs = ctx->problems.ptr;
   L.n_problems = n_problems;
   // Default chunk: about four grabs per resident warp (fine-grained enough to
@@ -406,7 +407,7 @@ int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, u
   if (st != MC_OK) return st;
   auto* ticket = reinterpret_cast<unsigned long long*>(static_cast<char*>(ctx->scratch.ptr) + kTicketOff);
   mci::SlabLaunch L{};
-  st = make_slab_launch(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, &L);
+  st = make_slab_launch(ctx, lcg, problems, n_problems, cfg, tally, rb, re, ticket, &L);
   if (st != MC_OK) return st;
   uint64_t key = 1469598103934665603ull;
   const void* ptrs[] = {ctx->problems.ptr, ctx->h_problems, tally->d_bins, tally->d_counts, tally->d_hist_state,
@@ -491,7 +492,7 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
   }
 
   mci::SlabLaunch L{};
-  st = make_slab_launch(ctx, lcg, n_problems, cfg, tally, rb, re, ticket, &L);
+  st = make_slab_launch(ctx, lcg, problems, n_problems, cfg, tally, rb, re, ticket, &L);
   if (st != MC_OK) return st;
   if (cfg->schedule == MC_SCHED_EVENT) {
     // Bank of up to 2^20 particles (about 100 MiB); allocated on first use.

@@ -167,6 +167,7 @@ extern "C" MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_proble
   }
   const bool stage = cfg->tally_mode == 1 || (cfg->tally_mode == 0 && tally->n_slots <= 8192);
   L.smem_slots = stage ? (uint32_t)tally->n_slots : 0u;
+  L.single_n_bins = n_problems == 1 ? problems[0].n_bins : 0u;
   L.f32 = cfg->precision == MC_FP32_GUARDED;
   L.block = cfg->block ? (int)cfg->block : 256;
   L.blocks_per_sm = (int)cfg->blocks_per_sm;

@@ -65,6 +65,7 @@ struct RunArgs {
   mcd::Lcg lcg;
   uint64_t event_cap;
   uint32_t smem_slots;
+  uint32_t smem_edges;  // single-problem launches: n_bins + 1 edges in shared memory (0: none)
 };
 
 // Per-lane counters for the lane's current problem.
@@ -115,6 +116,11 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
   if constexpr (SMEM) {
     for (uint32_t s = threadIdx.x; s < a.smem_slots; s += blockDim.x) s_tally[s] = 0ull;
   }
+  double* s_edges = a.smem_edges ? reinterpret_cast<double*>(s_tally + (SMEM ? a.smem_slots : 0u)) : nullptr;
+  if (s_edges) {
+    const SlabDev& p0 = a.probs[0];
+    for (uint32_t j = threadIdx.x; j < a.smem_edges; j += blockDim.x) s_edges[j] = mcs::slab_edge(p0, (int)j);
+  }
   __syncthreads();
 
   const unsigned kFull = 0xffffffffu;
@@ -132,7 +138,7 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
   const SlabDev* P = a.probs;
   mcs::Rng<M> r{0ull, 0ull};
   mcs::SlabParticle q{};
-  mcs::Sink sink{nullptr};
+  mcs::Sink sink{nullptr, s_edges};
   uint64_t gi = 0, events = 0;
 
   for (;;) {
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
 template <int M, bool F32, bool SMEM>
 int launch_history(const RunArgs& a, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
   auto k = slab_history_kernel<M, F32, SMEM>;
-  const size_t smem = SMEM ? (size_t)a.smem_slots * 8u : 0u;
+  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 8u;
   if (smem > 48u * 1024u) {
     int st = mci::cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               "cudaFuncSetAttribute(slab_history_kernel)");
@@ -284,6 +290,12 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
   a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
   a.event_cap = L.event_cap;
   a.smem_slots = L.smem_slots;
+  a.smem_edges = 0;
+  if (L.n_problems == 1) {
+    // one problem: its bin edges from a shared-memory table (the problem's
+    // bin count comes from the host copy through the launch descriptor)
+    if (L.single_n_bins + 1 <= 4096) a.smem_edges = L.single_n_bins + 1;
+  }
   if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
   return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
 }

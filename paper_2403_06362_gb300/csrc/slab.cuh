@@ -80,25 +80,47 @@ __device__ __forceinline__ double slab_edge(const SlabDev& p, int j) {
 
 __device__ __forceinline__ int clamp_bin(int j, int nb) { return j < 0 ? 0 : (j >= nb ? nb - 1 : j); }
 
-// Tally sink: shared-memory staging or direct global atomics.
+// Tally sink: shared-memory staging or direct global atomics, and an
+// optional table of the bin edges e_0..e_nb (shared memory; nullptr: each
+// edge is computed as j * h).
 struct Sink {
   unsigned long long* base;  // this history's [bin] row (smem or global)
+  const double* edges;
   __device__ __forceinline__ void add(int j, long long v) const {
     if (v != 0) atomicAdd(base + j, (unsigned long long)v);
   }
 };
 
-// Track length in every bin met by the segment [a, b] (a <= b) travelled
-// with 1/|mu| = w_mu: |[a,b] & [e_j, e_{j+1}]| * w_mu, to fixed point.
-__device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, double w_mu, const Sink& s) {
+// Order of two non-negative doubles from their bit patterns (IEEE-754
+// orders non-negative values like their bits read as integers): the fp64
+// comparisons of the path run on the integer pipes.
+__device__ __forceinline__ bool nn_lt(double a, double b) {
+  return __double_as_longlong(a) < __double_as_longlong(b);
+}
+
+__device__ __forceinline__ double edge_of(const SlabDev& p, const Sink& s, int j) {
+  return s.edges ? s.edges[j] : slab_edge(p, j);
+}
+
+// Track length in every bin met by the segment [a, b] (0 <= a <= b <= L):
+// |[a,b] & [e_j, e_{j+1}]| / |mu|, to fixed point.  w_fix = 2^32 / |mu|,
+// rounded once; since scaling by 2^32 commutes with rounding,
+// (hi - lo) * w_fix rounds to exactly 2^32 times the rounded
+// (hi - lo) * (1/|mu|).  The walk visits only the bins the segment
+// overlaps, starting from the one that holds a.
+__device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, double w_fix, const Sink& s) {
   const int nb = (int)p.n_bins;
-  const int j0 = clamp_bin((int)(a * p.inv_h) - 1, nb);
-  const int j1 = clamp_bin((int)(b * p.inv_h) + 1, nb);
-  for (int j = j0; j <= j1; ++j) {
-    const double lo_e = slab_edge(p, j), hi_e = slab_edge(p, j + 1);
-    const double lo = a > lo_e ? a : lo_e;
-    const double hi = b < hi_e ? b : hi_e;
-    if (hi > lo) s.add(j, __double2ll_rn(__dmul_rn(__dmul_rn(__dsub_rn(hi, lo), w_mu), kFix)));
+  int j = clamp_bin((int)(a * p.inv_h), nb);
+  while (j > 0 && nn_lt(a, edge_of(p, s, j))) --j;
+  while (j + 1 < nb && !nn_lt(a, edge_of(p, s, j + 1))) ++j;
+  double lo = a;
+  for (;;) {
+    const double e1 = edge_of(p, s, j + 1);
+    const double hi = nn_lt(b, e1) ? b : e1;
+    if (nn_lt(lo, hi)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(hi, lo), w_fix)));
+    if (!nn_lt(e1, b) || j + 1 >= nb) break;
+    lo = e1;
+    ++j;
   }
 }
 
@@ -151,12 +173,15 @@ __device__ __forceinline__ void point32(const SlabDev& p, float x, float d, cons
   s.add(j, fix32_from_float(d));
 }
 
-// Particle state of the slab physics.  fp64 path uses x, mu, w_mu; the
-// fp32 path keeps its geometry in xf, muf, wf.
+// Particle state of the slab physics.  fp64 path: x, mu and w_mu, which
+// holds 2^32 / |mu| (0 for mu = 0); the fp32 path keeps its geometry in
+// xf, muf and wf = 1 / |muf|.
 struct SlabParticle {
   double x, mu, w_mu;
   float xf, muf, wf;
 };
+
+__device__ __forceinline__ double fix_per_mu(double mu) { return mu != 0.0 ? __ddiv_rn(kFix, fabs(mu)) : 0.0; }
 
 // Outcome of a flight or a collision.
 enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3, kCollide = 4 };
@@ -165,7 +190,7 @@ enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3, kCo
 template <int M, bool F32>
 __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
   if (p.source == MC_SRC_BEAM) {
-    q.x = 0.0; q.mu = 1.0; q.w_mu = 1.0;
+    q.x = 0.0; q.mu = 1.0; q.w_mu = kFix;
     q.xf = 0.0f; q.muf = 1.0f; q.wf = 1.0f;
     return;
   }
@@ -174,7 +199,7 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
   if constexpr (!F32) {
     q.x = __dmul_rn(p.L, u1);
     q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
-    q.w_mu = q.mu != 0.0 ? __ddiv_rn(1.0, fabs(q.mu)) : 0.0;
+    q.w_mu = fix_per_mu(q.mu);
   } else {
     q.xf = p.L_f * (float)u1;
     q.muf = 2.0f * (float)u2 - 1.0f;
@@ -191,10 +216,14 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
   if constexpr (!F32) {
     const double d = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
     const double xn = __dadd_rn(q.x, __dmul_rn(d, q.mu));
-    if (q.mu > 0.0 && xn >= p.L) { seg64(p, q.x, p.L, q.w_mu, s); return kLeakHi; }
-    if (q.mu < 0.0 && xn <= 0.0) { seg64(p, 0.0, q.x, q.w_mu, s); return kLeakLo; }
-    if (q.mu == 0.0) point64(p, q.x, d, s);
-    else if (q.mu > 0.0) seg64(p, q.x, xn, q.w_mu, s);
+    // mu is never -0 (2u - 1 rounds an exact zero to +0), so its sign is the
+    // sign of its bit pattern; x, L and the positions of a forward flight are
+    // non-negative.
+    const long long mb = __double_as_longlong(q.mu);
+    if (mb > 0 && !nn_lt(xn, p.L)) { seg64(p, q.x, p.L, q.w_mu, s); return kLeakHi; }
+    if (mb < 0 && __double_as_longlong(xn) <= 0) { seg64(p, 0.0, q.x, q.w_mu, s); return kLeakLo; }
+    if (mb == 0) point64(p, q.x, d, s);
+    else if (mb > 0) seg64(p, q.x, xn, q.w_mu, s);
     else seg64(p, xn, q.x, q.w_mu, s);
     q.x = xn;
   } else {
@@ -230,11 +259,11 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
 // scattering into a new direction (kContinue).
 template <int M, bool F32>
 __device__ __forceinline__ int slab_collide(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
-  if (r.next(l) < p.p_abs) return kAbsorbed;
+  if (nn_lt(r.next(l), p.p_abs)) return kAbsorbed;  // u < 1 - c, both non-negative
   const double u2 = r.next(l);
   if constexpr (!F32) {
     q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
-    q.w_mu = q.mu != 0.0 ? __ddiv_rn(1.0, fabs(q.mu)) : 0.0;
+    q.w_mu = fix_per_mu(q.mu);
   } else {
     q.muf = 2.0f * (float)u2 - 1.0f;
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;

@@ -20,6 +20,7 @@ struct SlabLaunch {
   mc_lcg lcg;
   uint64_t event_cap;
   uint32_t smem_slots;         // 0 = global atomics; else slots staged in smem
+  uint32_t single_n_bins;      // n_bins of the problem when n_problems == 1
   bool f32;
   int block, blocks_per_sm, num_sms;
 };
