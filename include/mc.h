@@ -294,6 +294,16 @@ MC_API int mc_tally_read(mc_ctx* ctx, const mc_problem* problems, uint32_t probl
  * seed hash(i, s) of Eq. 4). */
 MC_API uint64_t mc_hash64(uint64_t k, uint64_t s);
 
+/* Diagnostics of the fp64 flight logarithm (no counterpart in the paper):
+ * the fp64 transport samples d = -ln(1 - u) / Sigma_t with a table-driven
+ * logarithm (Tang's method) that costs half the fp64 instructions of the
+ * CUDA library's.  mc_log1m evaluates it on the host (same code, same bits as
+ * the device); mc_log1m_device writes d_out[i] = ln(1 - d_u[i]) on the device
+ * with that logarithm (which = 0) or with the CUDA library's log (which = 1).
+ * u in [0, 1), a multiple of 2^-53.  Errors: MC_ERR_ARG, MC_ERR_CUDA. */
+MC_API double mc_log1m(double u);
+MC_API int mc_log1m_device(const double* d_u, double* d_out, uint64_t n, int which, void* stream);
+
 /* Section 5 normality procedure on host data x[n_batches][n_points]: the
  * normalised deviations z = (x - mean)/sd per point (sd with n-1) and the
  * Shapiro-Wilk W and p-value of each point's batch values (Royston's

@@ -95,6 +95,17 @@ def mc_hash64(k: int, s: int) -> int:
     return int(lib().mc_hash64(k, s))
 
 
+def mc_log1m(u: float) -> float:
+    """ln(1 - u) by the fp64 flight logarithm, evaluated on the host."""
+    return float(lib().mc_log1m(float(u)))
+
+
+def mc_log1m_device(d_u, d_out, which=0, stream=None):
+    """d_out = ln(1 - d_u) on the device: which 0 = the flight logarithm,
+    1 = the CUDA library's log (fp64 tensors of equal length)."""
+    return _ffi.check(lib().mc_log1m_device(_ptr(d_u), _ptr(d_out), d_u.numel(), which, _stream(stream)))
+
+
 def mc_seed_hash(ctx, lcg, parent_seed, key_begin, count, d_states, stream=None):
     return _ffi.check(lib().mc_seed_hash(ctx.handle, C.byref(lcg), parent_seed, key_begin, count,
                                        _ptr(d_states), _stream(stream)))

@@ -18,9 +18,9 @@ LIB = os.path.join(HERE, "libmc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
           "-I", CSRC, "-I", INCLUDE]
-NO_FMAD = {"slab.cu", "slab_event.cu", "box.cu", "box_event.cu", "pulse.cu"}
+NO_FMAD = {"slab.cu", "slab_event.cu", "box.cu", "box_event.cu", "pulse.cu", "diag.cu"}
 
 
 def _nvcc() -> str:
@@ -35,7 +35,7 @@ def sources():
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if not f.endswith(".pyc")]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)

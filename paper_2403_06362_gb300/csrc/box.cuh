@@ -224,7 +224,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
   bool collide;
   T d;
   if constexpr (sizeof(T) == 8) {
-    d = -log(1.0 - u) * b.inv_st[q.region];
+    d = -mclog::log1m(u) * b.inv_st[q.region];
     collide = d < ds;
   } else {
     d = -log1pf(-(float)u) * b.inv_st_f[q.region];
@@ -239,7 +239,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
       q64.region = q.region;
       int k64 = 0;
       const double ds64 = surface<double>(b, q64, k64);
-      const double d64 = -log(1.0 - u) * b.inv_st[q.region];
+      const double d64 = -mclog::log1m(u) * b.inv_st[q.region];
       collide = d64 < ds64;
       kind = k64;
     }

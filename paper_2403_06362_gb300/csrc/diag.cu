@@ -1,0 +1,36 @@
+// diag.cu -- diagnostic entry points: the flight logarithm of the fp64
+// transport path evaluated on the host and on the device, and the CUDA
+// library logarithm for comparison.  Not used by the transport itself.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "mc_log.cuh"
+
+namespace {
+
+__global__ void log1m_kernel(const double* __restrict__ u, double* __restrict__ out, uint64_t n, int which) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += nt) out[i] = which == 0 ? mclog::log1m(u[i]) : log(1.0 - u[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+MC_API double mc_log1m(double u) { return mclog::log1m(u); }
+
+MC_API int mc_log1m_device(const double* d_u, double* d_out, uint64_t n, int which, void* stream) {
+  if ((n && (!d_u || !d_out)) || (which != 0 && which != 1)) {
+    mci::set_error("mc_log1m_device: NULL buffer or which not in {0, 1}");
+    return MC_ERR_ARG;
+  }
+  if (n == 0) return MC_OK;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  log1m_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(d_u, d_out, n, which);
+  return mci::cuda_status(cudaGetLastError(), "log1m_kernel launch");
+}
+
+}  // extern "C"

@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "mc_log.cuh"
 #include "slab.cuh"
 #include "transport.h"
 
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
     } else {
       ++events;
       ++lc.flights;
-      const double d = -log(1.0 - r.next(l)) * P.inv_st;
+      const double d = -mclog::log1m(r.next(l)) * P.inv_st;
       const double tn = t + d;
       if (tn >= P.t_end) {
         ++lc.census;

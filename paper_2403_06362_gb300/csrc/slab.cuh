@@ -17,6 +17,7 @@
 
 #include "../../include/mc.h"
 #include "mc_device.cuh"
+#include "mc_log.cuh"
 
 namespace mcs {
 
@@ -214,7 +215,7 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
                                            const Sink& s) {
   const double u = r.next(l);
   if constexpr (!F32) {
-    const double d = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
+    const double d = __dmul_rn(-mclog::log1m(u), p.inv_st);
     const double xn = __dadd_rn(q.x, __dmul_rn(d, q.mu));
     // mu is never -0 (2u - 1 rounds an exact zero to +0), so its sign is the
     // sign of its bit pattern; x, L and the positions of a forward flight are
@@ -234,7 +235,7 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
     const bool near_lo = q.muf < 0.0f && fabsf(xn) <= p.guard_f;
     bool leak_hi = q.muf > 0.0f && xn >= p.L_f, leak_lo = q.muf < 0.0f && xn <= 0.0f;
     if (near_hi || near_lo) {
-      const double d64 = __dmul_rn(-log(__dsub_rn(1.0, u)), p.inv_st);
+      const double d64 = __dmul_rn(-mclog::log1m(u), p.inv_st);
       const double xn64 = __dadd_rn((double)q.xf, __dmul_rn(d64, (double)q.muf));
       leak_hi = q.muf > 0.0f && xn64 >= p.L;
       leak_lo = q.muf < 0.0f && xn64 <= 0.0;
