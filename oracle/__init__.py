@@ -19,14 +19,15 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mc_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "mc_oracle_box.c"), os.path.join(_HERE, "mc_oracle_azurv1.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "mc_oracle_box.c"), os.path.join(_HERE, "mc_oracle_azurv1.c"),
+         os.path.join(_HERE, "mc_oracle_census.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-NCOUNT = 16
+NCOUNT = 17
 COUNT_NAMES = [
     "source", "flights", "collisions", "absorptions", "scatters", "leak_lo", "leak_hi",
     "draws", "exceed_hist", "exceed_draws", "splits", "roulette_kills", "capped",
-    "max_draws", "children", "dropped",
+    "max_draws", "children", "dropped", "banked",
 ]
 SEED_HASH, SEED_STRIDE, SEED_HASH_HIER = 0, 1, 2
 SRC_ISOTROPIC, SRC_BEAM = 0, 1
@@ -71,7 +72,8 @@ class Azurv1Problem(C.Structure):
         ("sigma_t", C.c_double),
         ("seed", C.c_uint64), ("stride_q", C.c_uint64), ("id_offset", C.c_uint64), ("tally_offset", C.c_uint64),
         ("n_reps", C.c_uint32), ("n_batches", C.c_uint32), ("per_batch", C.c_uint32),
-        ("n_time_bins", C.c_uint32), ("seeding", C.c_uint32), ("pad", C.c_uint32),
+        ("n_time_bins", C.c_uint32), ("seeding", C.c_uint32), ("n_census", C.c_uint32),
+        ("pc_target", C.c_uint32), ("pad", C.c_uint32),
     ]
 
 
@@ -128,6 +130,8 @@ def lib():
             L.or_azurv1_seed.restype = u64; L.or_azurv1_seed.argtypes = [C.POINTER(Lcg), AP, u64]
             L.or_azurv1_run.restype = C.c_int
             L.or_azurv1_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, P, P]
+            L.or_azurv1_census_run.restype = C.c_int
+            L.or_azurv1_census_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, C.c_int, P]
             L.or_norm_cdf.restype = dbl; L.or_norm_cdf.argtypes = [dbl]
             L.or_norm_ppf.restype = dbl; L.or_norm_ppf.argtypes = [dbl]
             L.or_shapiro_wilk.restype = C.c_int
@@ -361,6 +365,26 @@ def azurv1_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, event_cap=2
     st = lib().or_azurv1_run(C.byref(lcg), C.byref(prob), g_begin, g_end, event_cap, _ptr(tally),
                              _ptr(counts), _ptr(hs), _ptr(hd))
     return dict(status=st, tally=tally, counts=counts, hist_state=hs, hist_draws=hd)
+
+
+def azurv1_census_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, event_cap=2**62, tally=None,
+                      counts=None, reverse=False, populations=False):
+    """Census phases with population control; g_begin, g_end on group
+    boundaries.  populations: also return the particles starting each phase,
+    per group ([groups, n_census])."""
+    total = int(prob.n_reps) * int(prob.n_batches) * int(prob.per_batch)
+    if g_end is None:
+        g_end = total
+    size = int(prob.tally_offset) + int(prob.n_reps) * int(prob.n_batches) * int(prob.n_time_bins)
+    if tally is None:
+        tally = np.zeros(size, dtype=np.int64)
+    if counts is None:
+        counts = np.zeros(NCOUNT, dtype=np.uint64)
+    groups = (g_end - g_begin) // int(prob.per_batch)
+    pop = np.zeros((groups, int(prob.n_census)), dtype=np.uint64) if populations else None
+    st = lib().or_azurv1_census_run(C.byref(lcg), C.byref(prob), g_begin, g_end, event_cap, _ptr(tally),
+                                    _ptr(counts), 1 if reverse else 0, _ptr(pop))
+    return dict(status=st, tally=tally, counts=counts, populations=pop)
 
 
 def azurv1_seed(lcg: Lcg, prob: Azurv1Problem, g: int) -> int:

@@ -53,6 +53,7 @@ enum {
     OR_C_MAX_DRAWS,
     OR_C_CHILDREN,
     OR_C_RESERVED,
+    OR_C_BANKED, /* census phases: particles banked at an intermediate census */
     OR_NCOUNT
 };
 
@@ -102,13 +103,21 @@ typedef struct {
     double c, nu, t_end, x_half, sigma_t;
     uint64_t seed, stride_q, id_offset, tally_offset;
     uint32_t n_reps, n_batches, per_batch, n_time_bins;
-    uint32_t seeding, pad;
+    uint32_t seeding;
+    uint32_t n_census;  /* >= 2: census phases with population control (mc_oracle_census.c) */
+    uint32_t pc_target; /* population per group after a control; 0 = per_batch */
+    uint32_t pad;
 } or_azurv1_problem;
 
 uint64_t or_azurv1_seed(const or_lcg* l, const or_azurv1_problem* a, uint64_t g);
 int or_azurv1_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
                   uint64_t event_cap, int64_t* tally, uint64_t* counts, uint64_t* hist_state,
                   uint64_t* hist_draws);
+
+/* Census phases with population control by one-off hashed values
+ * (mc_oracle_census.c); g_begin, g_end multiples of per_batch, hash seeding. */
+int or_azurv1_census_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
+                         uint64_t event_cap, int64_t* tally, uint64_t* counts, int reverse, uint64_t* pop);
 
 double or_norm_cdf(double z);
 double or_norm_ppf(double p);

@@ -193,13 +193,14 @@ def to_mc_box(b, mc):
 #           1000 source particles
 
 def azurv1(seeding=SEED_HASH_HIER, n_reps=30, n_batches=1000, per_batch=1000, c=0.4, nu=2.75, t_end=20.0,
-           x_half=1.0, n_time_bins=20, tally_offset=0, seed=None):
+           x_half=1.0, n_time_bins=20, tally_offset=0, seed=None, n_census=0, pc_target=0):
     if seed is None:
         seed = STRIDE_X0 if seeding == SEED_STRIDE else HASH_SEED
     return dict(c=float(c), nu=float(nu), t_end=float(t_end), x_half=float(x_half), sigma_t=1.0,
                 seed=int(seed), stride_q=STRIDE_Q, id_offset=0, tally_offset=int(tally_offset),
                 n_reps=int(n_reps), n_batches=int(n_batches), per_batch=int(per_batch),
-                n_time_bins=int(n_time_bins), seeding=int(seeding))
+                n_time_bins=int(n_time_bins), seeding=int(seeding), n_census=int(n_census),
+                pc_target=int(pc_target))
 
 
 def azurv1_histories(a):
@@ -215,7 +216,8 @@ def to_oracle_azurv1(a, oracle):
                                 sigma_t=a["sigma_t"], seed=a["seed"], stride_q=a["stride_q"],
                                 id_offset=a["id_offset"], tally_offset=a["tally_offset"],
                                 n_reps=a["n_reps"], n_batches=a["n_batches"], per_batch=a["per_batch"],
-                                n_time_bins=a["n_time_bins"], seeding=a["seeding"], pad=0)
+                                n_time_bins=a["n_time_bins"], seeding=a["seeding"],
+                                n_census=a.get("n_census", 0), pc_target=a.get("pc_target", 0), pad=0)
 
 
 def to_mc_pulse(a, mc):

@@ -1,0 +1,125 @@
+"""Pins of the oracle's census phases with population control by one-off
+hashed values (Section 4; the pulse problem of Section 5).
+
+Closed forms used (collision rate Sigma_t v = 1, k = c nu):
+  - without control the expected weighted collision density per source at
+    time t is exp((k - 1) t); unbiased control leaves every expectation
+    unchanged, so time bin j expects (exp((k-1)(j+1)) - exp((k-1) j))/(k-1);
+  - E[sum_i n_i] = N after every control (stochastic rounding of
+    w_i N / W);
+  - a pure absorber (c = 0) survives a phase of length T with probability
+    exp(-T), so E[banked per phase] = N exp(-T);
+and exact balances and order invariance (the property that lets a GPU bank
+particles in any order)."""
+import numpy as np
+import pytest
+
+from paper_2403_06362_gb300 import workloads as W
+
+K = 0.4 * 2.75
+
+
+def lcg(oracle):
+    return oracle.Lcg(m=63, pad=0, g=W.LCG_G, c=1)
+
+
+def counts(oracle, r):
+    return dict(zip(oracle.COUNT_NAMES, (int(v) for v in r["counts"])))
+
+
+def run(oracle, reverse=False, populations=False, **kw):
+    a = W.azurv1(**kw)
+    return a, oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle), reverse=reverse,
+                                       populations=populations)
+
+
+@pytest.mark.parametrize("seeding", [W.SEED_HASH_HIER, W.SEED_HASH])
+def test_exact_balances(oracle, seeding):
+    _, r = run(oracle, seeding=seeding, n_reps=2, n_batches=3, per_batch=400, n_census=8)
+    assert r["status"] == 0
+    c = counts(oracle, r)
+    assert c["source"] == 2400
+    # every flight ends in a collision, the census at t_end or a bank
+    assert c["flights"] == c["collisions"] + c["leak_hi"] + c["banked"]
+    assert c["collisions"] == c["absorptions"] + c["scatters"]
+    # particles: starts (sources, secondaries, extra copies) = ends
+    assert c["source"] + c["children"] + c["splits"] == c["absorptions"] + c["leak_hi"] + c["roulette_kills"]
+    # draws: a direction per source and secondary, one per flight, one per
+    # collision, multiplicity and new direction per scattering
+    assert c["draws"] == (c["source"] + c["children"]) + c["flights"] + c["collisions"] + 2 * c["scatters"]
+    assert c["roulette_kills"] > 0 and c["banked"] > 0
+
+
+def test_order_invariance_and_group_ranges(oracle):
+    a, fwd = run(oracle, n_reps=1, n_batches=6, per_batch=300, n_census=5)
+    _, rev = run(oracle, reverse=True, n_reps=1, n_batches=6, per_batch=300, n_census=5)
+    assert np.array_equal(fwd["tally"], rev["tally"])
+    assert np.array_equal(fwd["counts"], rev["counts"])
+    P = W.to_oracle_azurv1(a, oracle)
+    t = np.zeros_like(fwd["tally"])
+    c = np.zeros_like(fwd["counts"])
+    for lo, hi in [(0, 600), (600, 900), (900, 1800)]:
+        oracle.azurv1_census_run(lcg(oracle), P, lo, hi, tally=t, counts=c)
+    assert np.array_equal(t, fwd["tally"])
+    skip = oracle.COUNT_NAMES.index("max_draws")
+    assert np.array_equal(np.delete(c, skip), np.delete(fwd["counts"], skip))
+
+
+def test_rejects_stride_and_split_groups(oracle):
+    a = W.azurv1(seeding=W.SEED_STRIDE, n_reps=1, n_batches=2, per_batch=10, n_census=4)
+    assert oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle))["status"] == -1
+    a = W.azurv1(n_reps=1, n_batches=2, per_batch=10, n_census=4)
+    assert oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle), 0, 15)["status"] == -1
+
+
+def test_time_bins_unbiased_under_control(oracle):
+    # count every collision (x_half huge); 60 independent groups of 500
+    a, r = run(oracle, n_reps=1, n_batches=60, per_batch=500, x_half=1e300, n_census=20)
+    per_src = r["tally"].reshape(60, 20) * 2.0**-32 / 500
+    j = np.arange(20)
+    exp = (np.exp((K - 1) * (j + 1)) - np.exp((K - 1) * j)) / (K - 1)
+    se = per_src.std(axis=0, ddof=1) / np.sqrt(60)
+    assert np.all(np.abs(per_src.mean(axis=0) - exp) < 4.5 * se)
+
+
+def test_population_returns_to_target(oracle):
+    for target in (0, 250):
+        _, r = run(oracle, populations=True, n_reps=1, n_batches=40, per_batch=500, n_census=10,
+                   pc_target=target)
+        pop = r["populations"].astype(np.int64)
+        n = target or 500
+        assert np.all(pop[:, 0] == 500)
+        later = pop[:, 1:]
+        # stochastic rounding: E = n, variance <= (banked) / 4 <= about n / 3
+        dev = later - n
+        assert abs(dev.mean()) < 4.5 * np.sqrt(n / 3.0 / dev.size)
+        assert np.abs(dev).max() < 6 * np.sqrt(n / 3.0) + 1
+
+
+def test_pure_absorber_survival_per_phase(oracle):
+    # c = 0: no secondaries, a phase of length 2 is survived with prob e^-2
+    a, r = run(oracle, n_reps=1, n_batches=20, per_batch=1000, c=0.0, t_end=20.0, n_census=10)
+    c = counts(oracle, r)
+    assert c["children"] == 0 and c["scatters"] == 0
+    exp_banked = 20 * 9 * 1000 * np.exp(-2.0)
+    assert abs(c["banked"] - exp_banked) < 4.5 * np.sqrt(exp_banked)
+    exp_census = 20 * 1000 * np.exp(-2.0)
+    assert abs(c["leak_hi"] - exp_census) < 4.5 * np.sqrt(exp_census)
+    # with all weights 1 at the first census, a copy count is 0 or 1 only
+    # when the target is below the bank: here the bank (~135) is far below
+    # 1000, so every banked particle gets about 7 copies
+    assert c["splits"] > 5 * c["banked"]
+
+
+def test_window_flux_matches_the_uncontrolled_problem(oracle):
+    # both runs estimate the same flux in [-1, 1]: the census moves particles
+    # to their position at T_p, and control keeps the estimate unbiased
+    groups, per = 60, 500
+    _, ctl = run(oracle, n_reps=1, n_batches=groups, per_batch=per, n_census=20)
+    a0 = W.azurv1(n_reps=1, n_batches=groups, per_batch=per)
+    a0["seed"] = 4242  # independent streams
+    free = oracle.azurv1_run(lcg(oracle), W.to_oracle_azurv1(a0, oracle))
+    x = ctl["tally"].reshape(groups, 20) * 2.0**-32 / per
+    y = free["tally"].reshape(groups, 20) * 2.0**-32 / per
+    se = np.sqrt(x.var(axis=0, ddof=1) / groups + y.var(axis=0, ddof=1) / groups)
+    assert np.all(np.abs(x.mean(axis=0) - y.mean(axis=0)) < 4.5 * se)
