@@ -223,7 +223,7 @@ def main():
     ap.add_argument("--no-detail", action="store_true")
     ap.add_argument("--profile-workload", default=None,
                     choices=["slab_long_fp64", "slab_long_fp32", "slab_small_fp64", "box_fp32", "box_fp64",
-                             "batched_fp32", "pulse_hash", "pulse_stride"],
+                             "batched_fp32", "pulse_hash", "pulse_stride", "pulse_census"],
                     help="run one transport workload (a warm-up run, then one run) and exit; for profilers")
     ap.add_argument("--histories", type=int, default=0, help="history count for --profile-workload")
     args = ap.parse_args()
@@ -373,7 +373,10 @@ def profile_workload(args):
     name = args.profile_workload
     keep = None
     if name.startswith("pulse"):
-        a = W.azurv1(seeding=W.SEED_HASH_HIER if name.endswith("hash") else W.SEED_STRIDE)
+        if name == "pulse_census":
+            a = W.azurv1(seeding=W.SEED_HASH_HIER, n_census=20)
+        else:
+            a = W.azurv1(seeding=W.SEED_HASH_HIER if name.endswith("hash") else W.SEED_STRIDE)
         prob, keep = W.to_mc_pulse(a, mc)
         cp = mc.problem_array([prob])
         tally = mc.Tally(W.azurv1_tally_slots(a), 1)

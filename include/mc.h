@@ -166,10 +166,31 @@ typedef struct {
  * which case a history's secondaries draw from its one stream, depth-first.
  * Histories: n_reps * n_batches * per_batch; history g belongs to rep
  * g / (n_batches * per_batch) and batch (g / per_batch) % n_batches;
- * MC_SEED_HASH_HIER seeds it with hash(particle, hash(batch, hash(rep, s))). */
+ * MC_SEED_HASH_HIER seeds it with hash(particle, hash(batch, hash(rep, s))).
+ *
+ * Census phases (n_census >= 2; hash seeding only): time is cut into
+ * n_census equal phases, T_p = t_end p / n_census.  A particle reaching
+ * T_p < t_end is banked with its stream, direction and weight; at the end
+ * of each phase every (rep, batch) group's bank is population-controlled
+ * back toward pc_target particles (0 = per_batch): with W the exact sum of
+ * llrint(w 2^32) over the group's bank, particle i gets
+ * n_i = floor(w_i pc_target / (W 2^-32) + xi_i) copies of weight
+ * W 2^-32 / pc_target, where xi_i = (hash(2^63 + p, S_i) >> 11) 2^-53 is a
+ * one-off hashed value of the particle's state S_i (Section 4).  Copy 0
+ * continues the particle's stream, copy c >= 1 gets hash(c - 1, S_i) (Eq. 5).
+ * No decision depends on the order of the bank, so results are bit-identical
+ * in any schedule.  The history range must cover whole groups; per-history
+ * outputs and stride exceedance are not produced in this mode; counters add
+ * MC_C_BANKED (banked particles), MC_C_SPLITS (copies beyond the first) and
+ * MC_C_ROULETTE_KILLS (banked particles given no copy).  The two particle
+ * banks (48 bytes per particle, sized from the expected population) belong
+ * to the context; a full bank is reported as MC_ERR_CAPACITY by
+ * mc_tally_read. */
 typedef struct {
     double c, nu, t_end, x_half, sigma_t;
     uint32_t n_reps, n_batches, per_batch, n_time_bins;
+    uint32_t n_census;  /* phases; 0 or 1 = none                             */
+    uint32_t pc_target; /* population per group after a control; 0 = per_batch */
 } mc_pulse_spec;
 
 typedef struct {
@@ -215,6 +236,7 @@ enum {
     MC_C_LEAK_LO, MC_C_LEAK_HI, MC_C_DRAWS, MC_C_EXCEED_HIST, MC_C_EXCEED_DRAWS,
     MC_C_SPLITS, MC_C_ROULETTE_KILLS, MC_C_CAPPED, MC_C_MAX_DRAWS, MC_C_CHILDREN,
     MC_C_DROPPED, /* secondaries lost to a full bounded stack (MC_ERR_CAPACITY) */
+    MC_C_BANKED,  /* pulse census phases: particles banked at an intermediate census */
     MC_NCOUNT
 };
 

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-ffp-contract=off",
           "-I", CSRC, "-I", INCLUDE]
-NO_FMAD = {"slab.cu", "slab_event.cu", "box.cu", "box_event.cu", "pulse.cu", "diag.cu"}
+NO_FMAD = {"slab.cu", "slab_event.cu", "box.cu", "box_event.cu", "pulse.cu", "pulse_census.cu", "diag.cu"}
 
 
 def _nvcc() -> str:

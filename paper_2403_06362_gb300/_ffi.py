@@ -21,12 +21,12 @@ MC_SRC_ISOTROPIC, MC_SRC_BEAM = 0, 1
 MC_GEOM_SLAB, MC_GEOM_BOX, MC_GEOM_PULSE = 0, 1, 2
 MC_FP64, MC_FP32_GUARDED = 0, 1
 MC_SCHED_HISTORY, MC_SCHED_EVENT, MC_SCHED_AUTO = 0, 1, 2
-MC_NCOUNT = 16
+MC_NCOUNT = 17
 MC_BOX_MAX_GROUPS = 8
 COUNT_NAMES = [
     "source", "flights", "collisions", "absorptions", "scatters", "leak_lo", "leak_hi",
     "draws", "exceed_hist", "exceed_draws", "splits", "roulette_kills", "capped",
-    "max_draws", "children", "dropped",
+    "max_draws", "children", "dropped", "banked",
 ]
 
 EXPORTED = [
@@ -69,7 +69,8 @@ class mc_pulse_spec(C.Structure):
     _fields_ = [
         ("c", C.c_double), ("nu", C.c_double), ("t_end", C.c_double), ("x_half", C.c_double),
         ("sigma_t", C.c_double), ("n_reps", C.c_uint32), ("n_batches", C.c_uint32),
-        ("per_batch", C.c_uint32), ("n_time_bins", C.c_uint32),
+        ("per_batch", C.c_uint32), ("n_time_bins", C.c_uint32), ("n_census", C.c_uint32),
+        ("pc_target", C.c_uint32),
     ]
 
 

@@ -172,10 +172,14 @@ int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t*
                       ps->per_batch >= 1 && ps->n_time_bins >= 1 && q.n_bins == ps->n_time_bins &&
                       (uint64_t)q.n_batches == (uint64_t)ps->n_reps * ps->n_batches &&
                       q.n_histories == (uint64_t)ps->n_reps * ps->n_batches * ps->per_batch &&
-                      q.seeding <= MC_SEED_HASH_HIER && q.reserved == 0;
+                      q.seeding <= MC_SEED_HASH_HIER && q.reserved == 0 &&
+                      (ps->n_census < 2 || (q.seeding != MC_SEED_STRIDE && ps->n_census <= (1u << 20) &&
+                                            ps->pc_target <= (1u << 30) &&
+                                            (uint64_t)ps->n_reps * ps->n_batches < (1ull << 32)));
       if (!ok) {
         mci::set_error("problem %u: invalid pulse problem (one problem per call; spec, n_bins = n_time_bins, "
-                       "n_batches = reps * batches, n_histories = reps * batches * per_batch)", i);
+                       "n_batches = reps * batches, n_histories = reps * batches * per_batch; census phases "
+                       "need hash seeding, n_census <= 2^20, pc_target <= 2^30)", i);
         return MC_ERR_ARG;
       }
       const uint64_t slots = (uint64_t)q.n_bins * q.n_batches;
@@ -319,6 +323,7 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   if (ctx->h_done) cudaFreeHost(ctx->h_done);
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   ctx->children.release();
+  ctx->census.release();
   ctx->tune_tally.release();
   delete ctx->tune_cache;
   if (ctx->graphs) {
@@ -355,6 +360,11 @@ int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uin
   if (rb > re || re > *total) {
     mci::set_error("mc_transport_run: range [%llu, %llu) outside the %llu histories", (unsigned long long)rb,
                    (unsigned long long)re, (unsigned long long)*total);
+    return MC_ERR_ARG;
+  }
+  if (problems[0].geometry == MC_GEOM_PULSE && problems[0].pulse->n_census >= 2 &&
+      (rb % problems[0].pulse->per_batch != 0 || re % problems[0].pulse->per_batch != 0)) {
+    mci::set_error("pulse census phases: the history range must cover whole (rep, batch) groups");
     return MC_ERR_ARG;
   }
   return MC_OK;
@@ -488,7 +498,18 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     P.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 24);
     P.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 128;
     P.num_sms = ctx->num_sms;
-    return mci::pulse_run(P, s);
+    const mc_pulse_spec* ps = problems[0].pulse;
+    if (ps->n_census < 2) return mci::pulse_run(P, s);
+    mci::PulseCensusLaunch C{};
+    C.base = P;
+    C.spec = ps;
+    C.groups = (re - rb) / ps->per_batch;
+    C.group_begin = rb / ps->per_batch;
+    C.cap = mci::pulse_census_cap(*ps, C.groups);
+    st = ctx->census.reserve(mci::pulse_census_bytes(C.groups, C.cap));
+    if (st != MC_OK) return st;
+    C.d_buf = ctx->census.ptr;
+    return mci::pulse_census_run(C, s);
   }
 
   mci::SlabLaunch L{};

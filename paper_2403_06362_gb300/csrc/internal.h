@@ -60,6 +60,8 @@ struct mc_ctx {
   // Box transport: two banks of split children and a pinned count.
   mci::DeviceBuf children;
   unsigned long long* h_count = nullptr;
+  // Pulse census phases: bank counts, group weight totals and two banks.
+  mci::DeviceBuf census;
   // Private stream used only to capture graphs (the caller's stream may be
   // the legacy default stream, which cannot be captured).
   cudaStream_t capture_stream = nullptr;

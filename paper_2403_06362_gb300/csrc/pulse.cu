@@ -20,27 +20,16 @@
 
 #include "internal.h"
 #include "mc_log.cuh"
+#include "pulse.cuh"
 #include "slab.cuh"
 #include "transport.h"
 
 namespace {
 
-struct PulseDev {
-  double c, nu, t_end, x_half, sigma_t;
-  uint64_t n_hist, seed, stride_q, id_offset, tally_offset;
-  uint32_t n_reps, n_batches, per_batch, n_time_bins, seeding, pad;
-  // derived by pulse_prep_kernel
-  double inv_st;
-  long long unit;      // llrint(2^32 / Sigma_t): one collision-estimator score
-  uint64_t seed_hash;  // flat hash mode: seed half of hash(., s)
-};
-
-constexpr int kStack = 256;
-
-struct Pending {
-  double x, t;
-  uint64_t seed;
-};
+using mcp::kStack;
+using mcp::Pending;
+using mcp::PulseDev;
+using mcp::pulse_seed;
 
 struct PulseArgs {
   const PulseDev* prob;
@@ -61,16 +50,6 @@ __global__ void pulse_prep_kernel(PulseDev* p) {
     p->unit = __double2ll_rn(p->inv_st * mcs::kFix);
     p->seed_hash = mcd::seed_hash_of(p->seed);
   }
-}
-
-__device__ __forceinline__ uint64_t pulse_seed(const PulseDev& P, uint64_t g, const mcd::Affine* tab,
-                                               uint64_t mask) {
-  if (P.seeding == MC_SEED_STRIDE) return mcs::skip_tab(tab, P.seed, P.stride_q * (P.id_offset + g)) & mask;
-  if (P.seeding == MC_SEED_HASH) return mcd::hash_with(g, P.seed_hash) & mask;
-  const uint64_t pb = P.per_batch, nb = P.n_batches;
-  const uint64_t rep = g / (pb * nb), batch = (g / pb) % nb, part = g % pb;
-  const uint64_t h_rep = mcd::hash64(rep, P.seed);
-  return mcd::hash64(part, mcd::hash64(batch, h_rep)) & mask;
 }
 
 struct PulseCounts {
@@ -254,6 +233,8 @@ int pulse_fill_host(const mc_problem* src, void* dst) {
   q.per_batch = s->per_batch;
   q.n_time_bins = s->n_time_bins;
   q.seeding = src->seeding;
+  q.n_census = s->n_census;
+  q.pc_target = s->pc_target;
   std::memcpy(dst, &q, sizeof q);
   return MC_OK;
 }

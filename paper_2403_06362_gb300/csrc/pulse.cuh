@@ -1,0 +1,40 @@
+// pulse.cuh -- device record and seeds of the pulse problem (Section 5),
+// shared by the single-run kernel (pulse.cu) and the census-phase kernel
+// (pulse_census.cu).
+#pragma once
+#include <cstdint>
+
+#include "../../include/mc.h"
+#include "mc_device.cuh"
+#include "slab.cuh"
+
+namespace mcp {
+
+struct PulseDev {
+  double c, nu, t_end, x_half, sigma_t;
+  uint64_t n_hist, seed, stride_q, id_offset, tally_offset;
+  uint32_t n_reps, n_batches, per_batch, n_time_bins, seeding, n_census, pc_target, pad;
+  // derived by pulse_prep_kernel
+  double inv_st;
+  long long unit;      // llrint(2^32 / Sigma_t): one collision-estimator score
+  uint64_t seed_hash;  // flat hash mode: seed half of hash(., s)
+};
+
+constexpr int kStack = 256;
+
+struct Pending {
+  double x, t;
+  uint64_t seed;
+};
+
+__device__ __forceinline__ uint64_t pulse_seed(const PulseDev& P, uint64_t g, const mcd::Affine* tab,
+                                               uint64_t mask) {
+  if (P.seeding == MC_SEED_STRIDE) return mcs::skip_tab(tab, P.seed, P.stride_q * (P.id_offset + g)) & mask;
+  if (P.seeding == MC_SEED_HASH) return mcd::hash_with(g, P.seed_hash) & mask;
+  const uint64_t pb = P.per_batch, nb = P.n_batches;
+  const uint64_t rep = g / (pb * nb), batch = (g / pb) % nb, part = g % pb;
+  const uint64_t h_rep = mcd::hash64(rep, P.seed);
+  return mcd::hash64(part, mcd::hash64(batch, h_rep)) & mask;
+}
+
+}  // namespace mcp

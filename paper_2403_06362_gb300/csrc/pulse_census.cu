@@ -1,0 +1,368 @@
+// pulse_census.cu -- the pulse problem of Section 5 run in census phases,
+// with population control by one-off hashed values (Section 4) between
+// phases and on-demand seeds for the copies (Eq. 5).
+//
+// One launch per phase.  A lane takes a work item -- a source history in
+// the first phase, a banked particle afterwards -- and follows it, its
+// copies and all their secondaries depth-first until each is absorbed or
+// reaches the phase's census time.  A particle reaching the census is
+// appended to the next bank (one atomic per group of lanes that bank
+// together) and its weight, as int64 fixed point, is added to its group's
+// total.  The next launch turns each banked particle into
+//   n = floor(w N / W + xi),  xi = (hash(2^63 + p, S) >> 11) 2^-53
+// copies, with W the group's exact total; xi is a one-off value of the
+// particle's own state S.  Because n depends only on the particle and on
+// an exact integer sum, the order of the bank -- which atomics make
+// nondeterministic -- changes no result: tallies and counters are
+// bit-identical to the sequential definition.
+//
+// The host enqueues all phases without synchronising: each launch reads
+// the size of its input bank from device memory.
+// The fp64 arithmetic is rounded once per operation (--fmad=false).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+#include "mc_log.cuh"
+#include "pulse.cuh"
+#include "slab.cuh"
+#include "transport.h"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+using mcp::kStack;
+using mcp::Pending;
+using mcp::PulseDev;
+
+// A particle waiting at a census (48 bytes).
+struct BankRec {
+  double x, mu, w;
+  uint64_t s;      // LCG state, masked to m bits
+  uint64_t draws;  // draws made from this stream so far
+  uint32_t group;  // rep * n_batches + batch
+  uint32_t pad;
+};
+
+constexpr uint64_t kOneOffKey = 1ull << 63;  // keys of one-off values: 2^63 + phase
+
+struct CensusArgs {
+  const PulseDev* prob;
+  uint32_t phase;  // p = 1..C; the launch ends particles at T_p
+  int last;        // p == C: the census at T_p ends particles
+  double t0, tp;   // T_{p-1}, T_p
+  uint64_t range_begin, n_src;  // first phase: source histories
+  uint64_t group_begin;         // first group of the range
+  const BankRec* in;            // later phases: banked particles
+  const unsigned long long* in_count;
+  const long long* w_in;        // per group: exact weight total of `in`
+  BankRec* out;
+  unsigned long long* out_count;
+  unsigned long long* w_out;
+  uint64_t cap;
+  uint32_t chunk;
+  unsigned long long* ticket;
+  unsigned long long* tally;
+  unsigned long long* counts;
+  mcd::Lcg lcg;
+  uint64_t event_cap;
+};
+
+struct CensusCounts {
+  uint64_t src, flights, coll, absn, scat, census, children, capped, dropped, draws, maxd, banked, splits, kills;
+  __device__ void flush(unsigned long long* c) {
+    if (src) atomicAdd(c + MC_C_SOURCE, (unsigned long long)src);
+    if (flights) atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)flights);
+    if (coll) atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)coll);
+    if (absn) atomicAdd(c + MC_C_ABSORPTIONS, (unsigned long long)absn);
+    if (scat) atomicAdd(c + MC_C_SCATTERS, (unsigned long long)scat);
+    if (census) atomicAdd(c + MC_C_LEAK_HI, (unsigned long long)census);
+    if (children) atomicAdd(c + MC_C_CHILDREN, (unsigned long long)children);
+    if (capped) atomicAdd(c + MC_C_CAPPED, (unsigned long long)capped);
+    if (dropped) atomicAdd(c + MC_C_DROPPED, (unsigned long long)dropped);
+    if (draws) atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
+    if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
+    if (banked) atomicAdd(c + MC_C_BANKED, (unsigned long long)banked);
+    if (splits) atomicAdd(c + MC_C_SPLITS, (unsigned long long)splits);
+    if (kills) atomicAdd(c + MC_C_ROULETTE_KILLS, (unsigned long long)kills);
+  }
+  __device__ void stream_end(uint64_t d) {
+    draws += d;
+    if (d > maxd) maxd = d;
+  }
+};
+
+template <int M>
+__global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
+  __shared__ PulseDev sP;
+  if (threadIdx.x == 0) sP = *a.prob;
+  __syncthreads();
+  const PulseDev& P = sP;
+  const mcd::Lcg l = a.lcg;
+  const unsigned kFull = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const uint64_t total = a.in ? min((uint64_t)*a.in_count, a.cap) : a.n_src;
+  const double n_target = (double)(P.pc_target ? P.pc_target : P.per_batch);
+
+  Pending stack[kStack];
+  uint32_t sp = 0;
+  uint64_t pool_next = 0, pool_end = 0;
+  bool more = true, alive = false;
+  CensusCounts lc{};
+  mcs::Rng<M> r{0ull, 0ull};
+  double x = 0.0, t = 0.0, mu = 0.0, w = 1.0;
+  double x0 = 0.0, mu0 = 0.0;  // the banked particle whose copies this lane runs
+  uint64_t s0 = 0, copies_left = 0, next_key = 0, events = 0;
+  long long unit_w = 0;
+  uint32_t grp = 0;
+  unsigned long long* row = nullptr;
+
+  for (;;) {
+    unsigned dead = __ballot_sync(kFull, !alive);
+    while (dead != 0u && more) {
+      if (pool_next >= pool_end) {
+        unsigned long long b0 = 0;
+        if (lane == 0) b0 = atomicAdd(a.ticket, (unsigned long long)a.chunk);
+        b0 = __shfl_sync(kFull, b0, 0);
+        if (b0 >= total) { more = false; break; }
+        pool_next = b0;
+        pool_end = min((uint64_t)b0 + (uint64_t)a.chunk, total);
+      }
+      const uint64_t avail = pool_end - pool_next;
+      const unsigned rank = __popc(dead & lt_mask);
+      if (!alive && rank < avail) {
+        const uint64_t item = pool_next + rank;
+        if (a.in == nullptr) {
+          const uint64_t g = a.range_begin + item;
+          grp = (uint32_t)(g / P.per_batch);
+          r = mcs::Rng<M>{mcp::pulse_seed(P, g, nullptr, l.mask), 0ull};  // hash modes only
+          x = 0.0;
+          t = a.t0;
+          mu = 2.0 * r.next(l) - 1.0;
+          w = 1.0;
+          copies_left = 0;
+          ++lc.src;
+          alive = true;
+        } else {
+          const BankRec e = a.in[item];
+          grp = e.group;
+          const long long W = a.w_in[grp - a.group_begin];
+          uint64_t n = 0;
+          double wd = 0.0;
+          if (W > 0) {
+            wd = (double)W * 0x1p-32;
+            const double ratio = n_target / wd;
+            const double xi = (double)(mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11) * 0x1p-53;
+            n = (uint64_t)floor(e.w * ratio + xi);
+          }
+          if (n == 0) {
+            ++lc.kills;
+            lc.stream_end(e.draws);
+          } else {
+            lc.splits += n - 1;
+            w = wd / n_target;
+            x0 = e.x;
+            mu0 = e.mu;
+            s0 = e.s;
+            copies_left = n - 1;
+            next_key = 0;
+            r = mcs::Rng<M>{e.s, e.draws};
+            x = x0;
+            t = a.t0;
+            mu = mu0;
+            alive = true;
+          }
+        }
+        if (alive) {
+          row = a.tally + P.tally_offset + (uint64_t)grp * P.n_time_bins;
+          unit_w = __double2ll_rn(w * P.inv_st * mcs::kFix);
+          events = 0;
+          sp = 0;
+        }
+      }
+      pool_next += min((uint64_t)__popc(dead), avail);
+      dead = __ballot_sync(kFull, !alive);
+    }
+    if (__ballot_sync(kFull, alive) == 0u) break;
+    if (!alive) continue;
+
+    bool ended = false, banked = false;
+    if (events == a.event_cap) {
+      ++lc.capped;
+      ended = true;
+    } else {
+      ++events;
+      ++lc.flights;
+      const double d = -mclog::log1m(r.next(l)) * P.inv_st;
+      const double tn = t + d;
+      if (tn >= a.tp) {
+        ended = true;
+        if (a.last) {
+          ++lc.census;
+        } else {
+          banked = true;
+          ++lc.banked;
+          BankRec e;
+          e.x = x + (a.tp - t) * mu;
+          e.mu = mu;
+          e.w = w;
+          e.s = r.x & l.mask;
+          e.draws = r.draws;
+          e.group = grp;
+          e.pad = 0;
+          cg::coalesced_group cgp = cg::coalesced_threads();
+          unsigned long long base = 0;
+          if (cgp.thread_rank() == 0) base = atomicAdd(a.out_count, (unsigned long long)cgp.size());
+          base = cgp.shfl(base, 0);
+          const uint64_t idx = base + cgp.thread_rank();
+          if (idx < a.cap) a.out[idx] = e;
+          else ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
+          atomicAdd(a.w_out + (grp - a.group_begin), (unsigned long long)__double2ll_rn(w * mcs::kFix));
+        }
+      } else {
+        const double xn = x + d * mu;
+        ++lc.coll;
+        if (xn >= -P.x_half && xn <= P.x_half) {
+          uint32_t j = (uint32_t)floor(tn);
+          if (j >= P.n_time_bins) j = P.n_time_bins - 1;
+          atomicAdd(row + j, (unsigned long long)unit_w);
+        }
+        x = xn;
+        t = tn;
+        if (r.next(l) < P.c) {
+          ++lc.scat;
+          const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
+          for (uint32_t k = 0; k + 1 < n; ++k) {
+            if (sp < (uint32_t)kStack) {
+              stack[sp].x = x;
+              stack[sp].t = t;
+              stack[sp].seed = mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask;
+              ++sp;
+              ++lc.children;
+            } else {
+              ++lc.dropped;
+            }
+          }
+          mu = 2.0 * r.next(l) - 1.0;
+        } else {
+          ++lc.absn;
+          ended = true;
+        }
+      }
+    }
+    if (!ended) continue;
+    if (!banked) lc.stream_end(r.draws);
+    events = 0;
+    if (sp > 0) {  // next secondary of this family
+      --sp;
+      x = stack[sp].x;
+      t = stack[sp].t;
+      r = mcs::Rng<M>{stack[sp].seed, 0ull};
+      mu = 2.0 * r.next(l) - 1.0;
+      continue;
+    }
+    if (copies_left > 0) {  // next copy of the banked particle: Eq. (5) seed
+      --copies_left;
+      r = mcs::Rng<M>{mcd::hash64(next_key, s0) & l.mask, 0ull};
+      ++next_key;
+      x = x0;
+      t = a.t0;
+      mu = mu0;
+      continue;
+    }
+    alive = false;
+  }
+  lc.flush(a.counts);
+}
+
+// Census time T_p: 0, t_end p / C, t_end.
+double census_time(const mc_pulse_spec& s, uint32_t p) {
+  if (p == 0) return 0.0;
+  if (p >= s.n_census) return s.t_end;
+  return s.t_end * (double)p / (double)s.n_census;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+namespace mci {
+
+uint64_t pulse_census_cap(const mc_pulse_spec& s, uint64_t groups) {
+  const double k = s.c * s.nu;
+  const double growth = std::exp(std::max(0.0, k - 1.0) * s.sigma_t * (s.t_end / (double)s.n_census));
+  const double per = (double)std::max<uint32_t>(s.per_batch, s.pc_target ? s.pc_target : s.per_batch);
+  const double e = (double)groups * per * growth;
+  return (uint64_t)std::ceil(1.25 * e + 16.0 * std::sqrt(e)) + 4096;
+}
+
+size_t pulse_census_bytes(uint64_t groups, uint64_t cap) {
+  return 256 + 2 * align256(groups * sizeof(long long)) + 2 * align256(cap * sizeof(BankRec));
+}
+
+int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
+  const mc_pulse_spec& spec = *L.spec;
+  char* base = static_cast<char*>(L.d_buf);
+  auto* cnt = reinterpret_cast<unsigned long long*>(base);
+  const size_t wbytes = align256(L.groups * sizeof(long long));
+  long long* wsum[2] = {reinterpret_cast<long long*>(base + 256),
+                        reinterpret_cast<long long*>(base + 256 + wbytes)};
+  BankRec* bank[2] = {reinterpret_cast<BankRec*>(base + 256 + 2 * wbytes),
+                      reinterpret_cast<BankRec*>(base + 256 + 2 * wbytes + align256(L.cap * sizeof(BankRec)))};
+  auto k = L.base.lcg.m == 63 ? pulse_census_kernel<63> : pulse_census_kernel<0>;
+  int per_sm = 0;
+  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.base.block, 0),
+                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse census)");
+  if (st != MC_OK) return st;
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t full = (uint64_t)L.base.num_sms * (uint64_t)per_sm;
+
+  CensusArgs a{};
+  a.prob = static_cast<const PulseDev*>(L.base.d_prob);
+  a.range_begin = L.base.range_begin;
+  a.n_src = L.base.total;
+  a.group_begin = L.group_begin;
+  a.cap = L.cap;
+  a.chunk = L.base.chunk;
+  a.ticket = L.base.d_ticket;
+  a.tally = reinterpret_cast<unsigned long long*>(L.base.tally->d_bins);
+  a.counts = reinterpret_cast<unsigned long long*>(L.base.tally->d_counts);
+  a.lcg = mcd::Lcg{L.base.lcg.g, L.base.lcg.c, mcd::mask_of(L.base.lcg.m), L.base.lcg.m};
+  a.event_cap = L.base.event_cap;
+  const uint32_t C = spec.n_census;
+  for (uint32_t p = 1; p <= C; ++p) {
+    const int out = (int)((p - 1) & 1u), in = out ^ 1;
+    a.phase = p;
+    a.last = p == C;
+    a.t0 = census_time(spec, p - 1);
+    a.tp = census_time(spec, p);
+    a.in = p == 1 ? nullptr : bank[in];
+    a.in_count = cnt + in;
+    a.w_in = wsum[in];
+    a.out = bank[out];
+    a.out_count = cnt + out;
+    a.w_out = reinterpret_cast<unsigned long long*>(wsum[out]);
+    MC_TRY_CUDA(cudaMemsetAsync(L.base.d_ticket, 0, sizeof(unsigned long long), s));
+    if (!a.last) {
+      MC_TRY_CUDA(cudaMemsetAsync(cnt + out, 0, sizeof(unsigned long long), s));
+      MC_TRY_CUDA(cudaMemsetAsync(wsum[out], 0, L.groups * sizeof(long long), s));
+    }
+    uint64_t grid = full;
+    if (p == 1) {
+      const uint64_t warps = (a.n_src + a.chunk - 1) / a.chunk;
+      grid = std::max<uint64_t>(1, std::min<uint64_t>(full, (warps * 32 + L.base.block - 1) / L.base.block));
+    }
+    k<<<(int)grid, L.base.block, 0, s>>>(a);
+    st = cuda_status(cudaGetLastError(), "pulse_census_kernel launch");
+    if (st != MC_OK) return st;
+  }
+  return MC_OK;
+}
+
+}  // namespace mci

@@ -83,6 +83,19 @@ int pulse_fill_host(const mc_problem* src, void* dst);
 int pulse_prep(void* d_prob, cudaStream_t s);
 int pulse_run(const PulseLaunch& L, cudaStream_t s);
 
+// Census phases with population control (pulse_census.cu).  d_buf holds
+// pulse_census_bytes(groups, cap) bytes; the histories of `base` cover
+// whole groups starting at group_begin.
+struct PulseCensusLaunch {
+  PulseLaunch base;
+  const mc_pulse_spec* spec;
+  void* d_buf;
+  uint64_t groups, group_begin, cap;
+};
+uint64_t pulse_census_cap(const mc_pulse_spec& s, uint64_t groups);
+size_t pulse_census_bytes(uint64_t groups, uint64_t cap);
+int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s);
+
 size_t box_dev_size();
 size_t box_child_rec_size();
 int box_fill_host(const mc_problem* src, uint32_t n, void* dst);

@@ -226,7 +226,8 @@ def to_mc_pulse(a, mc):
     import ctypes
     spec = mc.mc_pulse_spec(c=a["c"], nu=a["nu"], t_end=a["t_end"], x_half=a["x_half"], sigma_t=a["sigma_t"],
                             n_reps=a["n_reps"], n_batches=a["n_batches"], per_batch=a["per_batch"],
-                            n_time_bins=a["n_time_bins"])
+                            n_time_bins=a["n_time_bins"], n_census=a.get("n_census", 0),
+                            pc_target=a.get("pc_target", 0))
     prob = mc.mc_problem(geometry=mc.MC_GEOM_PULSE, source=0, seeding=a["seeding"], n_bins=a["n_time_bins"],
                          n_batches=a["n_reps"] * a["n_batches"], reserved=0, L=0.0, sigma_t=a["sigma_t"],
                          c=a["c"], n_histories=azurv1_histories(a), seed=a["seed"], stride_q=a["stride_q"],

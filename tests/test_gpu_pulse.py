@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2403_06362_gb300 import workloads as W
+from paper_2403_06362_gb300._ffi import MC_NCOUNT
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +37,7 @@ def run_gpu(env, a, hist=True, **cfg):
 
 
 def counts_of(t):
-    return t.counts.cpu().numpy().view(np.uint64).reshape(-1, 16)[0]
+    return t.counts.cpu().numpy().view(np.uint64).reshape(-1, MC_NCOUNT)[0]
 
 
 def lcg(oracle):

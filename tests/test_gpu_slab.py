@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2403_06362_gb300 import workloads as W
+from paper_2403_06362_gb300._ffi import MC_NCOUNT
 
 pytestmark = pytest.mark.gpu
 
@@ -68,7 +69,7 @@ def assert_tally_close(got, exp):
 
 
 def counts_of(tally, n):
-    return tally.counts.cpu().numpy().view(np.uint64).reshape(n, 16)
+    return tally.counts.cpu().numpy().view(np.uint64).reshape(n, MC_NCOUNT)
 
 
 @pytest.mark.parametrize("seeding", [W.SEED_HASH, W.SEED_STRIDE, W.SEED_HASH_HIER])
