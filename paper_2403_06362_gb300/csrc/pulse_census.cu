@@ -51,6 +51,14 @@ struct BankRec {
 
 constexpr uint64_t kOneOffKey = 1ull << 63;  // keys of one-off values: 2^63 + phase
 
+// Per group, derived from the group's exact weight total W after a phase:
+// the factor N / (W 2^-32) of the copy counts (0 when W = 0: no copies),
+// the copies' weight W 2^-32 / N, its collision score and its fixed point.
+struct GroupCtl {
+  double ratio, w;
+  long long unit, wfix;
+};
+
 struct CensusArgs {
   const PulseDev* prob;
   uint32_t phase;  // p = 1..C; the launch ends particles at T_p
@@ -60,10 +68,10 @@ struct CensusArgs {
   uint64_t group_begin;         // first group of the range
   const BankRec* in;            // later phases: banked particles
   const unsigned long long* in_count;
-  const long long* w_in;        // per group: exact weight total of `in`
+  const GroupCtl* ctl;          // per group: control of `in`
   BankRec* out;
   unsigned long long* out_count;
-  unsigned long long* w_out;
+  unsigned long long* w_out;    // per group: exact weight total of `out`
   uint64_t cap;
   uint32_t chunk;
   unsigned long long* ticket;
@@ -108,7 +116,6 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint64_t total = a.in ? min((uint64_t)*a.in_count, a.cap) : a.n_src;
-  const double n_target = (double)(P.pc_target ? P.pc_target : P.per_batch);
 
   Pending stack[kStack];
   uint32_t sp = 0;
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
   double x = 0.0, t = 0.0, mu = 0.0, w = 1.0;
   double x0 = 0.0, mu0 = 0.0;  // the banked particle whose copies this lane runs
   uint64_t s0 = 0, copies_left = 0, next_key = 0, events = 0;
-  long long unit_w = 0;
+  long long unit_w = 0, wfix = 0;  // collision score and fixed-point weight of w
   uint32_t grp = 0;
   unsigned long long* row = nullptr;
 
@@ -146,27 +153,25 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           t = a.t0;
           mu = 2.0 * r.next(l) - 1.0;
           w = 1.0;
+          unit_w = P.unit;
+          wfix = (long long)mcs::kFix;
           copies_left = 0;
           ++lc.src;
           alive = true;
         } else {
           const BankRec e = a.in[item];
           grp = e.group;
-          const long long W = a.w_in[grp - a.group_begin];
-          uint64_t n = 0;
-          double wd = 0.0;
-          if (W > 0) {
-            wd = (double)W * 0x1p-32;
-            const double ratio = n_target / wd;
-            const double xi = (double)(mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11) * 0x1p-53;
-            n = (uint64_t)floor(e.w * ratio + xi);
-          }
+          const GroupCtl gc = a.ctl[grp - a.group_begin];
+          const double xi = (double)(mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11) * 0x1p-53;
+          const uint64_t n = (uint64_t)floor(e.w * gc.ratio + xi);
           if (n == 0) {
             ++lc.kills;
             lc.stream_end(e.draws);
           } else {
             lc.splits += n - 1;
-            w = wd / n_target;
+            w = gc.w;
+            unit_w = gc.unit;
+            wfix = gc.wfix;
             x0 = e.x;
             mu0 = e.mu;
             s0 = e.s;
@@ -181,7 +186,6 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
         }
         if (alive) {
           row = a.tally + P.tally_offset + (uint64_t)grp * P.n_time_bins;
-          unit_w = __double2ll_rn(w * P.inv_st * mcs::kFix);
           events = 0;
           sp = 0;
         }
@@ -223,7 +227,10 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           const uint64_t idx = base + cgp.thread_rank();
           if (idx < a.cap) a.out[idx] = e;
           else ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
-          atomicAdd(a.w_out + (grp - a.group_begin), (unsigned long long)__double2ll_rn(w * mcs::kFix));
+          // lanes of one group carry one weight in a phase: one atomic per group
+          cg::coalesced_group same = cg::labeled_partition(cgp, grp);
+          if (same.thread_rank() == 0)
+            atomicAdd(a.w_out + (grp - a.group_begin), (unsigned long long)(wfix * (long long)same.size()));
         }
       } else {
         const double xn = x + d * mu;
@@ -281,6 +288,26 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
   lc.flush(a.counts);
 }
 
+// Control of each group after a phase: GroupCtl from the exact weight
+// total, which is then cleared for the next phase.
+__global__ void census_control_kernel(const PulseDev* __restrict__ prob, unsigned long long* __restrict__ wsum,
+                                      GroupCtl* __restrict__ ctl, uint64_t groups) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= groups) return;
+  const double n_target = (double)(prob->pc_target ? prob->pc_target : prob->per_batch);
+  const long long W = (long long)wsum[i];
+  GroupCtl g{0.0, 0.0, 0, 0};
+  if (W > 0) {
+    const double wd = (double)W * 0x1p-32;
+    g.ratio = n_target / wd;
+    g.w = wd / n_target;
+    g.unit = __double2ll_rn(g.w * prob->inv_st * mcs::kFix);
+    g.wfix = __double2ll_rn(g.w * mcs::kFix);
+  }
+  ctl[i] = g;
+  wsum[i] = 0ull;
+}
+
 // Census time T_p: 0, t_end p / C, t_end.
 double census_time(const mc_pulse_spec& s, uint32_t p) {
   if (p == 0) return 0.0;
@@ -303,18 +330,21 @@ uint64_t pulse_census_cap(const mc_pulse_spec& s, uint64_t groups) {
 }
 
 size_t pulse_census_bytes(uint64_t groups, uint64_t cap) {
-  return 256 + 2 * align256(groups * sizeof(long long)) + 2 * align256(cap * sizeof(BankRec));
+  return 256 + align256(groups * sizeof(long long)) + align256(groups * sizeof(GroupCtl)) +
+         2 * align256(cap * sizeof(BankRec));
 }
 
 int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   const mc_pulse_spec& spec = *L.spec;
   char* base = static_cast<char*>(L.d_buf);
   auto* cnt = reinterpret_cast<unsigned long long*>(base);
-  const size_t wbytes = align256(L.groups * sizeof(long long));
-  long long* wsum[2] = {reinterpret_cast<long long*>(base + 256),
-                        reinterpret_cast<long long*>(base + 256 + wbytes)};
-  BankRec* bank[2] = {reinterpret_cast<BankRec*>(base + 256 + 2 * wbytes),
-                      reinterpret_cast<BankRec*>(base + 256 + 2 * wbytes + align256(L.cap * sizeof(BankRec)))};
+  size_t off = 256;
+  auto* wsum = reinterpret_cast<unsigned long long*>(base + off);
+  off += align256(L.groups * sizeof(long long));
+  auto* ctl = reinterpret_cast<GroupCtl*>(base + off);
+  off += align256(L.groups * sizeof(GroupCtl));
+  BankRec* bank[2] = {reinterpret_cast<BankRec*>(base + off),
+                      reinterpret_cast<BankRec*>(base + off + align256(L.cap * sizeof(BankRec)))};
   auto k = L.base.lcg.m == 63 ? pulse_census_kernel<63> : pulse_census_kernel<0>;
   int per_sm = 0;
   int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.base.block, 0),
@@ -336,6 +366,7 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   a.lcg = mcd::Lcg{L.base.lcg.g, L.base.lcg.c, mcd::mask_of(L.base.lcg.m), L.base.lcg.m};
   a.event_cap = L.base.event_cap;
   const uint32_t C = spec.n_census;
+  MC_TRY_CUDA(cudaMemsetAsync(wsum, 0, L.groups * sizeof(long long), s));
   for (uint32_t p = 1; p <= C; ++p) {
     const int out = (int)((p - 1) & 1u), in = out ^ 1;
     a.phase = p;
@@ -344,15 +375,12 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
     a.tp = census_time(spec, p);
     a.in = p == 1 ? nullptr : bank[in];
     a.in_count = cnt + in;
-    a.w_in = wsum[in];
+    a.ctl = ctl;
     a.out = bank[out];
     a.out_count = cnt + out;
-    a.w_out = reinterpret_cast<unsigned long long*>(wsum[out]);
+    a.w_out = wsum;
     MC_TRY_CUDA(cudaMemsetAsync(L.base.d_ticket, 0, sizeof(unsigned long long), s));
-    if (!a.last) {
-      MC_TRY_CUDA(cudaMemsetAsync(cnt + out, 0, sizeof(unsigned long long), s));
-      MC_TRY_CUDA(cudaMemsetAsync(wsum[out], 0, L.groups * sizeof(long long), s));
-    }
+    if (!a.last) MC_TRY_CUDA(cudaMemsetAsync(cnt + out, 0, sizeof(unsigned long long), s));
     uint64_t grid = full;
     if (p == 1) {
       const uint64_t warps = (a.n_src + a.chunk - 1) / a.chunk;
@@ -361,6 +389,11 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
     k<<<(int)grid, L.base.block, 0, s>>>(a);
     st = cuda_status(cudaGetLastError(), "pulse_census_kernel launch");
     if (st != MC_OK) return st;
+    if (!a.last) {
+      census_control_kernel<<<(unsigned)((L.groups + 255) / 256), 256, 0, s>>>(a.prob, wsum, ctl, L.groups);
+      st = cuda_status(cudaGetLastError(), "census_control_kernel launch");
+      if (st != MC_OK) return st;
+    }
   }
   return MC_OK;
 }
