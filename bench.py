@@ -43,6 +43,7 @@ DRAWS = 64
 # funnel shift, shift, exponent multiply-add, add (5); range flag for the
 # exact redo (1); 64-bit digest add (2).
 OPS_PER_DRAW = 14
+E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 # DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
 # the ncu capture summarised in profiles/draw_digest_m63_kernel_rng_microbench.md
 # (mean of the hash and stride launches).  Set to None when the kernel changes.
@@ -309,19 +310,38 @@ def main():
                 "peak_note": f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {RECIPE_SM_MAX_MHZ:.0f} MHz",
                 "ops_per_draw": OPS_PER_DRAW}
 
-    # End to end through the public call: device results copied to pinned
-    # host memory inside the timed region, every step.
+    # End to end through the public call: every final state and digest is
+    # copied to pinned host memory inside the timed region, every step.  The
+    # id range of each mode is cut into slices (mc_lcg_draw takes any id
+    # range); a copy stream drains slice j while the launch stream computes
+    # slice j + 1, and a slice is recomputed only after its previous copy has
+    # finished.  The device-to-host link (about 190 GB/s measured on this
+    # machine) bounds the result.
     h_st = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
     h_dg = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
     e2e_steps = max(3, min(20, args.steps))
+    sl = n // E2E_SLICES
+    copy_stream = torch.cuda.Stream(device=dev)
+    copied = [[None] * E2E_SLICES for _ in specs]
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(e2e_steps):
         for i in range(2):
-            launch(i)
-            h_st[i].copy_(st[i], non_blocking=True)
-            h_dg[i].copy_(dg[i], non_blocking=True)
+            for j in range(E2E_SLICES):
+                lo, hi = j * sl, (j + 1) * sl
+                if copied[i][j] is not None:
+                    stream.wait_event(copied[i][j])
+                mc.mc_lcg_draw(ctx, lcg, specs[i], id0 + lo, st[i][lo:hi], sl, DRAWS, None, dg[i][lo:hi], stream)
+                done = torch.cuda.Event()
+                done.record(stream)
+                copy_stream.wait_event(done)
+                with torch.cuda.stream(copy_stream):
+                    h_st[i][lo:hi].copy_(st[i][lo:hi], non_blocking=True)
+                    h_dg[i][lo:hi].copy_(dg[i][lo:hi], non_blocking=True)
+                    copied[i][j] = torch.cuda.Event()
+                    copied[i][j].record(copy_stream)
+    stream.wait_stream(copy_stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
@@ -331,7 +351,8 @@ def main():
         e2e_ms = float(t.item())
     e2e = {"value": draws_per_step / (e2e_ms / 1e3), "unit": "draws/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": 2 * 2 * n * 8,
-           "note": "inputs are scalars (seed, id range); every final state and digest is copied to host"}
+           "note": "inputs are scalars (seed, id range); every final state and digest is copied to host, "
+                   f"in {E2E_SLICES} id slices per mode overlapped with the draw kernels"}
 
     detail = {"draws_per_s_hash": n * DRAWS * world / (statistics.mean(t_hash) / 1e3),
               "draws_per_s_stride": n * DRAWS * world / (statistics.mean(t_str) / 1e3),
@@ -373,10 +394,12 @@ def profile_workload(args):
     name = args.profile_workload
     keep = None
     if name.startswith("pulse"):
+        # --histories N: N // 10^6 repetitions of 1000 x 1000 (default 30)
+        reps = max(1, args.histories // 10**6) if args.histories else 30
         if name == "pulse_census":
-            a = W.azurv1(seeding=W.SEED_HASH_HIER, n_census=20)
+            a = W.azurv1(seeding=W.SEED_HASH_HIER, n_census=20, n_reps=reps)
         else:
-            a = W.azurv1(seeding=W.SEED_HASH_HIER if name.endswith("hash") else W.SEED_STRIDE)
+            a = W.azurv1(seeding=W.SEED_HASH_HIER if name.endswith("hash") else W.SEED_STRIDE, n_reps=reps)
         prob, keep = W.to_mc_pulse(a, mc)
         cp = mc.problem_array([prob])
         tally = mc.Tally(W.azurv1_tally_slots(a), 1)
@@ -531,8 +554,11 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
     # Section 5 experiment: 30 repetitions x 1000 batches x 1000 sources, hash
     # (hierarchical seeds) vs stride; Shapiro-Wilk on each of the 20 points
     # over the 1000 batch means, per repetition (600 tests per mode)
-    for sname, sd in (("hash", W.SEED_HASH_HIER), ("stride", W.SEED_STRIDE)):
-        a = W.azurv1(seeding=sd)
+    # ("census_hash": the same with 20 census phases and population control
+    # by one-off hashed values back to 1000 per batch at every census)
+    for sname, sd, nc in (("hash", W.SEED_HASH_HIER, 0), ("stride", W.SEED_STRIDE, 0),
+                          ("census_hash", W.SEED_HASH_HIER, 20)):
+        a = W.azurv1(seeding=sd, n_census=nc)
         prob, spec = W.to_mc_pulse(a, mc)
         cp = mc.problem_array([prob])
         tally = mc.Tally(W.azurv1_tally_slots(a), 1)
@@ -553,9 +579,15 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             "ms": ms, "source_histories_per_s": n / (ms / 1e3), "collisions_per_s": r.counts["collisions"] / (ms / 1e3),
             "census_per_source": r.counts["leak_hi"] / n, "secondaries": r.counts["children"],
             "sw_fails_p_lt_0.05": int(np.sum(pvals < 0.05)), "sw_tests": int(pvals.size),
-            "sw_median_p_per_point": [float(v) for v in np.median(pvals, axis=0)],
-            "paper_fails_context": {"hash": "339/600", "stride": "369/600"}[sname],
-            "paper_runtime_context": {"hash": "111.46 s (serial Python)", "stride": "113.26 s (serial Python)"}[sname]}
+            "sw_median_p_per_point": [float(v) for v in np.median(pvals, axis=0)]}
+        if nc:
+            res[f"pulse_paper_{sname}"].update(
+                n_census=nc, flights=r.counts["flights"], banked=r.counts["banked"],
+                copies_beyond_first=r.counts["splits"], no_copy=r.counts["roulette_kills"])
+        else:
+            res[f"pulse_paper_{sname}"].update(
+                paper_fails_context={"hash": "339/600", "stride": "369/600"}[sname],
+                paper_runtime_context={"hash": "111.46 s (serial Python)", "stride": "113.26 s (serial Python)"}[sname])
         del spec
 
     # 3D two-region box, 10^8 source histories
