@@ -219,7 +219,7 @@ typedef struct {
                             /* (AUTO: the mc_autotune choice, cached per shape)   */
     uint32_t precision;     /* MC_FP64 or MC_FP32_GUARDED (flight and geometry)   */
     uint32_t block;         /* threads per block; 0 = library default             */
-    uint32_t chunk;         /* histories a warp takes per ticket grab; 0 = 128    */
+    uint32_t chunk;         /* histories a warp takes per ticket grab; 0 = default */
     uint32_t blocks_per_sm; /* 0 = from the occupancy calculator                  */
     uint32_t use_graph;     /* 1 = capture the launch sequence once and replay    */
     uint32_t accumulate;    /* 0 = zero tallies and counts first; 1 = add to them */
@@ -228,6 +228,12 @@ typedef struct {
     uint64_t event_cap;     /* per-history flight cap; 0 = 2^40                   */
     uint64_t range_begin;   /* run only global histories [begin,end) of the       */
     uint64_t range_end;     /* concatenated problems; end 0 = all                 */
+    uint32_t stack_depth;   /* pulse problem: pending secondaries a lane keeps    */
+                            /* (1..256, 0 = 256); in hash modes the rest wait in  */
+                            /* a device overflow bank processed after the launch  */
+                            /* (their streams depend only on their seeds, Eq. 5); */
+                            /* stride mode counts them in MC_C_DROPPED            */
+    uint32_t reserved2;     /* must be 0                                           */
 } mc_run_config;
 
 /* Counter block per problem: uint64_t[MC_NCOUNT], exact integers. */

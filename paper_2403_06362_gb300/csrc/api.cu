@@ -324,6 +324,7 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   ctx->children.release();
   ctx->census.release();
+  ctx->overflow.release();
   ctx->tune_tally.release();
   delete ctx->tune_cache;
   if (ctx->graphs) {
@@ -352,8 +353,9 @@ int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uin
   st = check_problems(problems, n_problems, tally, total);
   if (st != MC_OK) return st;
   if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
-      (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512))) {
-    mci::set_error("mc_transport_run: bad run config (schedule/precision/tally_mode/block)");
+      (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512)) || cfg->stack_depth > 256 ||
+      cfg->reserved2 != 0) {
+    mci::set_error("mc_transport_run: bad run config (schedule/precision/tally_mode/block/stack_depth)");
     return MC_ERR_ARG;
   }
   const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? *total : cfg->range_end;
@@ -498,6 +500,16 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     P.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 24);
     P.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 128;
     P.num_sms = ctx->num_sms;
+    P.stack_depth = cfg->stack_depth ? cfg->stack_depth : 256u;
+    if (problems[0].seeding != MC_SEED_STRIDE) {
+      // overflow bank of 2^20 secondaries (32 MiB per generation bank)
+      P.ovf_cap = 1ull << 20;
+      st = ctx->overflow.reserve(mci::pulse_ovf_bytes(P.ovf_cap));
+      if (st != MC_OK) return st;
+      if (!ctx->h_count) MC_TRY_CUDA(cudaMallocHost(&ctx->h_count, sizeof(unsigned long long)));
+      P.d_ovf = ctx->overflow.ptr;
+      P.h_count = ctx->h_count;
+    }
     const mc_pulse_spec* ps = problems[0].pulse;
     if (ps->n_census < 2) return mci::pulse_run(P, s);
     mci::PulseCensusLaunch C{};

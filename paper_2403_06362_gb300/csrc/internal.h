@@ -60,6 +60,9 @@ struct mc_ctx {
   // Box transport: two banks of split children and a pinned count.
   mci::DeviceBuf children;
   unsigned long long* h_count = nullptr;
+  // Pulse problem: two generation banks of secondaries that overflowed the
+  // lane stacks (hash modes).
+  mci::DeviceBuf overflow;
   // Pulse census phases: bank counts, group weight totals and two banks.
   mci::DeviceBuf census;
   // Private stream used only to capture graphs (the caller's stream may be

@@ -27,6 +27,7 @@
 namespace {
 
 using mcp::kStack;
+using mcp::Overflow;
 using mcp::Pending;
 using mcp::PulseDev;
 using mcp::pulse_seed;
@@ -42,6 +43,12 @@ struct PulseArgs {
   uint64_t* hist_draws;
   mcd::Lcg lcg;
   uint64_t event_cap;
+  uint32_t stack_depth;            // pending secondaries a lane keeps (<= kStack)
+  const Overflow* ovf_in;          // non-null: the work items are overflowed secondaries
+  const unsigned long long* ovf_in_count;
+  Overflow* ovf_out;               // non-null (hash modes): where secondaries beyond the stack go
+  unsigned long long* ovf_out_count;
+  uint64_t ovf_cap;
 };
 
 __global__ void pulse_prep_kernel(PulseDev* p) {
@@ -96,7 +103,9 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
   mcs::Rng<M> r{0ull, 0ull};
   double x = 0.0, t = 0.0, mu = 0.0;
   uint64_t gi = 0, events = 0, fam_draws = 0;
+  uint32_t grp = 0;
   unsigned long long* row = nullptr;
+  const uint64_t total = a.ovf_in ? min((uint64_t)*a.ovf_in_count, a.ovf_cap) : a.total;
 
   for (;;) {
     unsigned dead = __ballot_sync(kFull, !alive);
@@ -105,15 +114,30 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
         unsigned long long b0 = 0;
         if (lane == 0) b0 = atomicAdd(a.ticket, (unsigned long long)a.chunk);
         b0 = __shfl_sync(kFull, b0, 0);
-        if (b0 >= a.total) { more = false; break; }
+        if (b0 >= total) { more = false; break; }
         pool_next = b0;
-        pool_end = min((uint64_t)b0 + (uint64_t)a.chunk, (uint64_t)a.total);
+        pool_end = min((uint64_t)b0 + (uint64_t)a.chunk, total);
       }
       const uint64_t avail = pool_end - pool_next;
       const unsigned rank = __popc(dead & lt_mask);
-      if (!alive && rank < avail) {
+      if (!alive && rank < avail && a.ovf_in) {
+        // an overflowed secondary: hash seeded, it starts a family of its own
+        const Overflow e = a.ovf_in[pool_next + rank];
+        grp = e.group;
+        row = a.tally + P.tally_offset + (uint64_t)grp * P.n_time_bins;
+        r = mcs::Rng<M>{e.seed, 0ull};
+        x = e.x;
+        t = e.t;
+        mu = 2.0 * r.next(l) - 1.0;
+        events = 0;
+        fam_draws = 0;
+        sp = 0;
+        primary = false;
+        alive = true;
+      } else if (!alive && rank < avail) {
         gi = a.range_begin + pool_next + rank;
-        row = a.tally + P.tally_offset + (gi / P.per_batch) * P.n_time_bins;
+        grp = (uint32_t)(gi / P.per_batch);
+        row = a.tally + P.tally_offset + (uint64_t)grp * P.n_time_bins;
         r = mcs::Rng<M>{pulse_seed(P, gi, tab, l.mask), 0ull};
         x = 0.0;
         t = 0.0;
@@ -157,12 +181,21 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
           ++lc.scat;
           const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
           for (uint32_t k = 0; k + 1 < n; ++k) {
-            if (sp < (uint32_t)kStack) {
+            const uint64_t seed = hash_mode ? (mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask) : 0ull;
+            if (sp < a.stack_depth) {
               stack[sp].x = x;
               stack[sp].t = t;
-              stack[sp].seed = hash_mode ? (mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask) : 0ull;
+              stack[sp].seed = seed;
               ++sp;
               ++lc.children;
+            } else if (a.ovf_out) {  // hash modes only
+              const unsigned long long idx = atomicAdd(a.ovf_out_count, 1ull);
+              if (idx < a.ovf_cap) {
+                a.ovf_out[idx] = Overflow{x, t, seed, grp, 0u};
+                ++lc.children;
+              } else {
+                ++lc.dropped;
+              }
             } else {
               ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
             }
@@ -257,17 +290,58 @@ int pulse_run(const PulseLaunch& L, cudaStream_t s) {
   a.hist_draws = L.tally->d_hist_draws;
   a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
   a.event_cap = L.event_cap;
+  a.stack_depth = L.stack_depth;
   auto k = L.lcg.m == 63 ? pulse_kernel<63> : pulse_kernel<0>;
   int per_sm = 0;
   int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
                        "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");
   if (st != MC_OK) return st;
   if (per_sm < 1) per_sm = 1;
+  const uint64_t full = (uint64_t)L.num_sms * per_sm;
   const uint64_t warps_needed = (a.total + a.chunk - 1) / a.chunk;
   const uint64_t blocks_needed = (warps_needed * 32 + L.block - 1) / L.block;
-  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)L.num_sms * per_sm, blocks_needed));
+  const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(full, blocks_needed));
+  if (!L.d_ovf) {
+    k<<<grid, L.block, 0, s>>>(a);
+    return cuda_status(cudaGetLastError(), "pulse_kernel launch");
+  }
+  // Hash modes: secondaries beyond the lane stacks go to an overflow bank,
+  // processed generation by generation until a generation overflows nothing.
+  auto* cnt = static_cast<unsigned long long*>(L.d_ovf);
+  Overflow* bank[2] = {reinterpret_cast<Overflow*>(static_cast<char*>(L.d_ovf) + 256),
+                       reinterpret_cast<Overflow*>(static_cast<char*>(L.d_ovf) + 256 + L.ovf_cap * sizeof(Overflow))};
+  a.ovf_cap = L.ovf_cap;
+  a.ovf_out = bank[0];
+  a.ovf_out_count = cnt;
+  MC_TRY_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
   k<<<grid, L.block, 0, s>>>(a);
-  return cuda_status(cudaGetLastError(), "pulse_kernel launch");
+  st = cuda_status(cudaGetLastError(), "pulse_kernel launch");
+  for (int gen = 1; st == MC_OK; ++gen) {
+    const int cur = (gen - 1) & 1, nxt = cur ^ 1;
+    MC_TRY_CUDA(cudaMemcpyAsync(L.h_count, cnt + cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    MC_TRY_CUDA(cudaStreamSynchronize(s));
+    const uint64_t made = std::min<uint64_t>(*L.h_count, L.ovf_cap);
+    if (made == 0) break;
+    if (gen > 100000) {
+      set_error("pulse transport: more than 100000 generations of overflowed secondaries");
+      return MC_ERR_TIMEOUT;
+    }
+    PulseArgs b = a;
+    b.ovf_in = bank[cur];
+    b.ovf_in_count = cnt + cur;
+    b.ovf_out = bank[nxt];
+    b.ovf_out_count = cnt + nxt;
+    b.total = made;
+    MC_TRY_CUDA(cudaMemsetAsync(cnt + nxt, 0, sizeof(unsigned long long), s));
+    MC_TRY_CUDA(cudaMemsetAsync(L.d_ticket, 0, sizeof(unsigned long long), s));
+    const uint64_t w = (made + a.chunk - 1) / a.chunk;
+    const int g2 = (int)std::max<uint64_t>(1, std::min<uint64_t>(full, (w * 32 + L.block - 1) / L.block));
+    k<<<g2, L.block, 0, s>>>(b);
+    st = cuda_status(cudaGetLastError(), "pulse_kernel launch (overflow)");
+  }
+  return st;
 }
+
+size_t pulse_ovf_bytes(uint64_t cap) { return 256 + 2 * cap * sizeof(Overflow); }
 
 }  // namespace mci

@@ -27,6 +27,15 @@ struct Pending {
   uint64_t seed;
 };
 
+// A hash-seeded secondary that did not fit on its lane's stack (32 bytes):
+// it waits in a device bank for a later launch of the same phase.
+struct Overflow {
+  double x, t;
+  uint64_t seed;
+  uint32_t group;  // rep * n_batches + batch: its tally row
+  uint32_t pad;
+};
+
 __device__ __forceinline__ uint64_t pulse_seed(const PulseDev& P, uint64_t g, const mcd::Affine* tab,
                                                uint64_t mask) {
   if (P.seeding == MC_SEED_STRIDE) return mcs::skip_tab(tab, P.seed, P.stride_q * (P.id_offset + g)) & mask;

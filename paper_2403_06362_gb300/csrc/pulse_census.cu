@@ -16,8 +16,10 @@
 // nondeterministic -- changes no result: tallies and counters are
 // bit-identical to the sequential definition.
 //
-// The host enqueues all phases without synchronising: each launch reads
-// the size of its input bank from device memory.
+// The host enqueues the phases back to back (each launch reads the size of
+// its input bank from device memory); it waits only to read how many
+// secondaries overflowed the lane stacks in a phase, and launches the
+// generations of those before the phase's control.
 // The fp64 arithmetic is rounded once per operation (--fmad=false).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -37,6 +39,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 using mcp::kStack;
+using mcp::Overflow;
 using mcp::Pending;
 using mcp::PulseDev;
 
@@ -79,6 +82,12 @@ struct CensusArgs {
   unsigned long long* counts;
   mcd::Lcg lcg;
   uint64_t event_cap;
+  uint32_t stack_depth;            // pending secondaries a lane keeps (<= kStack)
+  const Overflow* ovf_in;          // non-null: the work items are overflowed secondaries
+  const unsigned long long* ovf_in_count;
+  Overflow* ovf_out;               // where secondaries beyond the stack go
+  unsigned long long* ovf_out_count;
+  uint64_t ovf_cap;
 };
 
 struct CensusCounts {
@@ -115,7 +124,8 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
   const unsigned kFull = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const uint64_t total = a.in ? min((uint64_t)*a.in_count, a.cap) : a.n_src;
+  const uint64_t total = a.ovf_in ? min((uint64_t)*a.ovf_in_count, a.ovf_cap)
+                                  : (a.in ? min((uint64_t)*a.in_count, a.cap) : a.n_src);
 
   Pending stack[kStack];
   uint32_t sp = 0;
@@ -145,7 +155,27 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
       const unsigned rank = __popc(dead & lt_mask);
       if (!alive && rank < avail) {
         const uint64_t item = pool_next + rank;
-        if (a.in == nullptr) {
+        if (a.ovf_in) {
+          // an overflowed secondary of this phase: the phase's group weight
+          const Overflow e = a.ovf_in[item];
+          grp = e.group;
+          if (a.phase == 1) {
+            w = 1.0;
+            unit_w = P.unit;
+            wfix = (long long)mcs::kFix;
+          } else {
+            const GroupCtl gc = a.ctl[grp - a.group_begin];
+            w = gc.w;
+            unit_w = gc.unit;
+            wfix = gc.wfix;
+          }
+          r = mcs::Rng<M>{e.seed, 0ull};
+          x = e.x;
+          t = e.t;
+          mu = 2.0 * r.next(l) - 1.0;
+          copies_left = 0;
+          alive = true;
+        } else if (a.in == nullptr) {
           const uint64_t g = a.range_begin + item;
           grp = (uint32_t)(g / P.per_batch);
           r = mcs::Rng<M>{mcp::pulse_seed(P, g, nullptr, l.mask), 0ull};  // hash modes only
@@ -246,14 +276,21 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           ++lc.scat;
           const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
           for (uint32_t k = 0; k + 1 < n; ++k) {
-            if (sp < (uint32_t)kStack) {
+            const uint64_t seed = mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask;
+            if (sp < a.stack_depth) {
               stack[sp].x = x;
               stack[sp].t = t;
-              stack[sp].seed = mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask;
+              stack[sp].seed = seed;
               ++sp;
               ++lc.children;
             } else {
-              ++lc.dropped;
+              const unsigned long long idx = atomicAdd(a.ovf_out_count, 1ull);
+              if (idx < a.ovf_cap) {
+                a.ovf_out[idx] = Overflow{x, t, seed, grp, 0u};
+                ++lc.children;
+              } else {
+                ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
+              }
             }
           }
           mu = 2.0 * r.next(l) - 1.0;
@@ -365,6 +402,12 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   a.counts = reinterpret_cast<unsigned long long*>(L.base.tally->d_counts);
   a.lcg = mcd::Lcg{L.base.lcg.g, L.base.lcg.c, mcd::mask_of(L.base.lcg.m), L.base.lcg.m};
   a.event_cap = L.base.event_cap;
+  a.stack_depth = L.base.stack_depth;
+  auto* ocnt = static_cast<unsigned long long*>(L.base.d_ovf);
+  Overflow* obank[2] = {
+      reinterpret_cast<Overflow*>(static_cast<char*>(L.base.d_ovf) + 256),
+      reinterpret_cast<Overflow*>(static_cast<char*>(L.base.d_ovf) + 256 + L.base.ovf_cap * sizeof(Overflow))};
+  a.ovf_cap = L.base.ovf_cap;
   const uint32_t C = spec.n_census;
   MC_TRY_CUDA(cudaMemsetAsync(wsum, 0, L.groups * sizeof(long long), s));
   for (uint32_t p = 1; p <= C; ++p) {
@@ -386,9 +429,38 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
       const uint64_t warps = (a.n_src + a.chunk - 1) / a.chunk;
       grid = std::max<uint64_t>(1, std::min<uint64_t>(full, (warps * 32 + L.base.block - 1) / L.base.block));
     }
+    a.ovf_in = nullptr;
+    a.ovf_out = obank[0];
+    a.ovf_out_count = ocnt;
+    MC_TRY_CUDA(cudaMemsetAsync(ocnt, 0, 2 * sizeof(unsigned long long), s));
     k<<<(int)grid, L.base.block, 0, s>>>(a);
     st = cuda_status(cudaGetLastError(), "pulse_census_kernel launch");
     if (st != MC_OK) return st;
+    // secondaries that overflowed the lane stacks, generation by generation
+    for (int gen = 1;; ++gen) {
+      const int cur = (gen - 1) & 1, nxt = cur ^ 1;
+      MC_TRY_CUDA(cudaMemcpyAsync(L.base.h_count, ocnt + cur, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  s));
+      MC_TRY_CUDA(cudaStreamSynchronize(s));
+      if (*L.base.h_count == 0) break;
+      if (gen > 100000) {
+        set_error("pulse census: more than 100000 generations of overflowed secondaries");
+        return MC_ERR_TIMEOUT;
+      }
+      CensusArgs b = a;
+      b.ovf_in = obank[cur];
+      b.ovf_in_count = ocnt + cur;
+      b.ovf_out = obank[nxt];
+      b.ovf_out_count = ocnt + nxt;
+      MC_TRY_CUDA(cudaMemsetAsync(ocnt + nxt, 0, sizeof(unsigned long long), s));
+      MC_TRY_CUDA(cudaMemsetAsync(L.base.d_ticket, 0, sizeof(unsigned long long), s));
+      const uint64_t made = std::min<uint64_t>(*L.base.h_count, L.base.ovf_cap);
+      const uint64_t w = (made + a.chunk - 1) / a.chunk;
+      const uint64_t g2 = std::max<uint64_t>(1, std::min<uint64_t>(full, (w * 32 + L.base.block - 1) / L.base.block));
+      k<<<(int)g2, L.base.block, 0, s>>>(b);
+      st = cuda_status(cudaGetLastError(), "pulse_census_kernel launch (overflow)");
+      if (st != MC_OK) return st;
+    }
     if (!a.last) {
       census_control_kernel<<<(unsigned)((L.groups + 255) / 256), 256, 0, s>>>(a.prob, wsum, ctl, L.groups);
       st = cuda_status(cudaGetLastError(), "census_control_kernel launch");

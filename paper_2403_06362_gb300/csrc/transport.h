@@ -76,7 +76,14 @@ struct PulseLaunch {
   mc_lcg lcg;
   uint64_t event_cap;
   int block, num_sms;
+  uint32_t stack_depth;          // 1..256
+  // Overflow bank (hash modes; pulse_ovf_bytes(ovf_cap) bytes; nullptr: a
+  // full stack drops, MC_ERR_CAPACITY) and a pinned count for the host loop.
+  void* d_ovf;
+  uint64_t ovf_cap;
+  unsigned long long* h_count;
 };
+size_t pulse_ovf_bytes(uint64_t cap);
 
 size_t pulse_dev_size();
 int pulse_fill_host(const mc_problem* src, void* dst);

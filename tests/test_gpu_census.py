@@ -120,3 +120,12 @@ def test_census_full_experiment_sampled_groups(env, oracle):
     # control holds each group near its target: the census at t_end counts
     # about N e^{0.1} per group instead of N e^{2} without control
     assert abs(c["leak_hi"] / W.azurv1_histories(a) - np.exp(0.1)) < 0.01
+
+
+@pytest.mark.parametrize("depth", [1, 3])
+def test_census_overflow_bank_keeps_the_bits(env, oracle, depth):
+    a = W.azurv1(n_reps=1, n_batches=6, per_batch=300, n_census=5)
+    t = run_gpu(env, a, stack_depth=depth)
+    o = oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle))
+    assert np.array_equal(bins_of(t), o["tally"])
+    assert names(oracle, counts_of(t)) == names(oracle, o["counts"])

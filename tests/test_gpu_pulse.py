@@ -88,3 +88,41 @@ def test_pulse_bits_independent_of_launch_shape(env, block, chunk):
     t = run_gpu(env, a, hist=False, block=block, chunk=chunk)
     assert np.array_equal(base.bins.cpu().numpy(), t.bins.cpu().numpy())
     assert np.array_equal(counts_of(base), counts_of(t))
+
+
+@pytest.mark.parametrize("seeding,depth", [(W.SEED_HASH_HIER, 1), (W.SEED_HASH, 2), (W.SEED_HASH_HIER, 8)])
+def test_pulse_overflow_bank_keeps_the_bits(env, oracle, seeding, depth):
+    """Lane stacks of 1, 2 or 8 pending secondaries: the rest wait in the
+    device overflow bank and run in later launches; hash-seeded secondaries
+    depend only on their seeds (Eq. 5), so every result equals the oracle's
+    (whose stack is unbounded)."""
+    a = W.azurv1(seeding=seeding, n_reps=2, n_batches=10, per_batch=300)
+    t = run_gpu(env, a, stack_depth=depth)
+    o = oracle.azurv1_run(lcg(oracle), W.to_oracle_azurv1(a, oracle), per_history=True)
+    assert np.array_equal(t.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(t.hist_draws.cpu().numpy().view(np.uint64), o["hist_draws"])
+    gc, oc = counts_of(t), o["counts"]
+    assert np.array_equal(gc[:15], oc[:15]) and gc[15] == 0
+    assert np.array_equal(t.bins.cpu().numpy().view(np.int64), o["tally"])
+
+
+def test_pulse_stride_stack_overflow_is_reported(env):
+    """Stride mode cannot defer a secondary (the family shares one stream in
+    depth-first order): a full stack drops it and mc_tally_read reports
+    MC_ERR_CAPACITY."""
+    mc, ctx, _ = env
+    a = W.azurv1(seeding=W.SEED_STRIDE, n_reps=1, n_batches=4, per_batch=200)
+    t = run_gpu(env, a, stack_depth=1)
+    assert int(counts_of(t)[15]) > 0
+    prob, spec = W.to_mc_pulse(a, mc)
+    arr = mc.problem_array([prob])
+    with pytest.raises(mc.McError):
+        mc.mc_tally_read(ctx, arr, 0, t.c)
+    del spec
+
+
+def test_pulse_rejects_bad_stack_depth(env):
+    mc, _, _ = env
+    a = W.azurv1(n_reps=1, n_batches=2, per_batch=10)
+    with pytest.raises(mc.McError):
+        run_gpu(env, a, stack_depth=257)
