@@ -512,6 +512,10 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     }
     const mc_pulse_spec* ps = problems[0].pulse;
     if (ps->n_census < 2) return mci::pulse_run(P, s);
+    if (rb % ps->per_batch != 0 || re % ps->per_batch != 0) {  // (also checked by validate_run)
+      mci::set_error("pulse census phases: the history range must cover whole (rep, batch) groups");
+      return MC_ERR_ARG;
+    }
     mci::PulseCensusLaunch C{};
     C.base = P;
     C.spec = ps;
@@ -580,8 +584,13 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
   t2.d_counts = reinterpret_cast<uint64_t*>(static_cast<char*>(ctx->tune_tally.ptr) + bins);
   // A sample from the middle of the concatenated history list: all of it up
   // to 2^17 histories, else a quarter (at least 2^17).
-  const uint64_t S = total <= (1ull << 17) ? total : std::max<uint64_t>(1ull << 17, total / 4);
-  const uint64_t start = (total - S) / 2;
+  uint64_t S = total <= (1ull << 17) ? total : std::max<uint64_t>(1ull << 17, total / 4);
+  uint64_t start = (total - S) / 2;
+  if (problems[0].geometry == MC_GEOM_PULSE) {  // whole (rep, batch) groups (census phases need them)
+    const uint64_t pb = problems[0].pulse->per_batch;
+    start -= start % pb;
+    S = std::min<uint64_t>(total - start, (S + pb - 1) / pb * pb);
+  }
   struct Cand { uint32_t schedule, block, chunk, graph; };
   const bool box = problems[0].geometry == MC_GEOM_BOX;
   // Chunks relative to the default for the full run (histories per warp

@@ -129,3 +129,17 @@ def test_census_overflow_bank_keeps_the_bits(env, oracle, depth):
     o = oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle))
     assert np.array_equal(bins_of(t), o["tally"])
     assert names(oracle, counts_of(t)) == names(oracle, o["counts"])
+
+
+def test_census_autotune_uses_whole_groups(env, oracle):
+    mc, ctx, torch = env
+    a = W.azurv1(n_reps=1, n_batches=7, per_batch=250, n_census=4)
+    prob, spec = W.to_mc_pulse(a, mc)
+    arr = mc.problem_array([prob])
+    t = mc.Tally(W.azurv1_tally_slots(a), 1)
+    mc.mc_autotune(ctx, mc.make_lcg(), arr, mc.mc_run_config(), t.c)
+    mc.mc_transport_run(ctx, mc.make_lcg(), arr, mc.mc_run_config(schedule=mc.MC_SCHED_AUTO), t.c)
+    torch.cuda.synchronize()
+    o = oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle))
+    assert np.array_equal(bins_of(t), o["tally"])
+    del spec
