@@ -332,6 +332,18 @@ MC_API uint64_t mc_hash64(uint64_t k, uint64_t s);
 MC_API double mc_log1m(double u);
 MC_API int mc_log1m_device(const double* d_u, double* d_out, uint64_t n, int which, void* stream);
 
+/* Diagnostics of the fp64 steps the transport computes on the integer pipes
+ * (no counterpart in the paper): mc_recip_rn(y) is 1/y rounded to nearest
+ * even, exactly as IEEE division, built from an fp32 estimate, two integer
+ * Newton steps and an exact remainder (host evaluation of the device code);
+ * mc_recip_rn_device writes d_out[i] = 1/d_y[i] with it (which = 0) or with
+ * the CUDA division (which = 1); mc_two_u_minus_1(n) is 2u - 1 for the
+ * uniform u = n 2^-53 (n < 2^53; 0 otherwise).  Errors: MC_ERR_ARG,
+ * MC_ERR_CUDA. */
+MC_API double mc_recip_rn(double y);
+MC_API double mc_two_u_minus_1(uint64_t n);
+MC_API int mc_recip_rn_device(const double* d_y, double* d_out, uint64_t n, int which, void* stream);
+
 /* Section 5 normality procedure on host data x[n_batches][n_points]: the
  * normalised deviations z = (x - mean)/sd per point (sd with n-1) and the
  * Shapiro-Wilk W and p-value of each point's batch values (Royston's

@@ -106,6 +106,22 @@ def mc_log1m_device(d_u, d_out, which=0, stream=None):
     return _ffi.check(lib().mc_log1m_device(_ptr(d_u), _ptr(d_out), d_u.numel(), which, _stream(stream)))
 
 
+def mc_recip_rn(y: float) -> float:
+    """1/y rounded to nearest, by the integer-pipe reciprocal (host evaluation)."""
+    return float(lib().mc_recip_rn(float(y)))
+
+
+def mc_two_u_minus_1(n: int) -> float:
+    """2u - 1 for u = n 2^-53, assembled from integer operations (host evaluation)."""
+    return float(lib().mc_two_u_minus_1(int(n)))
+
+
+def mc_recip_rn_device(d_y, d_out, which=0, stream=None):
+    """d_out = 1/d_y on the device: which 0 = the integer-pipe reciprocal,
+    1 = the CUDA division (fp64 tensors of equal length)."""
+    return _ffi.check(lib().mc_recip_rn_device(_ptr(d_y), _ptr(d_out), d_y.numel(), which, _stream(stream)))
+
+
 def mc_seed_hash(ctx, lcg, parent_seed, key_begin, count, d_states, stream=None):
     return _ffi.check(lib().mc_seed_hash(ctx.handle, C.byref(lcg), parent_seed, key_begin, count,
                                        _ptr(d_states), _stream(stream)))

@@ -32,7 +32,8 @@ COUNT_NAMES = [
 EXPORTED = [
     "mc_last_error", "mc_ctx_create", "mc_ctx_destroy", "mc_seed_hash", "mc_seed_stride",
     "mc_lcg_draw", "mc_transport_run", "mc_tally_read", "mc_hash64", "mc_normality",
-    "mc_transport_run_static", "mc_autotune", "mc_log1m", "mc_log1m_device",
+    "mc_transport_run_static", "mc_autotune", "mc_log1m", "mc_log1m_device", "mc_recip_rn",
+    "mc_two_u_minus_1", "mc_recip_rn_device",
 ]
 
 
@@ -123,6 +124,9 @@ def _load():
         "mc_normality": (i32, [P, u32, u32, P, P, P]),
         "mc_log1m": (dbl, [dbl]),
         "mc_log1m_device": (i32, [P, P, u64, i32, P]),
+        "mc_recip_rn": (dbl, [dbl]),
+        "mc_two_u_minus_1": (dbl, [u64]),
+        "mc_recip_rn_device": (i32, [P, P, u64, i32, P]),
         "mc_autotune": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_problem), u32, C.POINTER(mc_run_config),
                               C.POINTER(mc_tally), C.POINTER(mc_run_config), C.POINTER(C.c_float), P]),
         "mc_transport_run_static": (i32, [C.POINTER(mc_lcg), C.POINTER(mc_problem), u32,

@@ -67,9 +67,16 @@ template <typename T> __device__ __forceinline__ T sel(const double& d, const fl
 template <> __device__ __forceinline__ double sel<double>(const double& d, const float&) { return d; }
 template <> __device__ __forceinline__ float sel<float>(const double&, const float& f) { return f; }
 
+template <typename T> __device__ __forceinline__ T recip(T v);
+template <> __device__ __forceinline__ double recip<double>(double v) { return mcx::recip_rn(v); }
+template <> __device__ __forceinline__ float recip<float>(float v) { return 1.0f / v; }
+
+// Componentwise inverse of the direction (fp64: the correctly rounded
+// reciprocal on the integer pipes, fp_exact.cuh).
 template <typename T>
 __device__ __forceinline__ void set_inv(Part<T>& q) {
-  for (int a = 0; a < 3; ++a) q.inv[a] = q.u[a] != T(0) ? T(1) / q.u[a] : T(0);
+#pragma unroll 1
+  for (int a = 0; a < 3; ++a) q.inv[a] = q.u[a] != T(0) ? recip<T>(q.u[a]) : T(0);
 }
 
 // Marsaglia (1972): v1, v2 uniform on [-1,1)^2 until v1^2 + v2^2 < 1.
@@ -77,8 +84,13 @@ template <int M, typename T>
 __device__ __forceinline__ void iso_dir(mcs::Rng<M>& r, const mcd::Lcg& l, T u[3]) {
   T v1, v2, s;
   do {
-    v1 = T(2) * from_u<T>(r.next(l)) - T(1);
-    v2 = T(2) * from_u<T>(r.next(l)) - T(1);
+    if constexpr (sizeof(T) == 8) {  // 2u - 1 exactly, on the integer pipes
+      v1 = mcx::two_u_minus_1(r.next_n(l));
+      v2 = mcx::two_u_minus_1(r.next_n(l));
+    } else {
+      v1 = T(2) * from_u<T>(r.next(l)) - T(1);
+      v2 = T(2) * from_u<T>(r.next(l)) - T(1);
+    }
     s = v1 * v1 + v2 * v2;
   } while (s >= T(1));
   const T t = sqrt(T(1) - s);
@@ -234,7 +246,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
       for (int a = 0; a < 3; ++a) {
         q64.p[a] = q.p[a];
         q64.u[a] = q.u[a];
-        q64.inv[a] = q.inv[a] != 0.0f ? 1.0 / (double)q.u[a] : 0.0;
+        q64.inv[a] = q.inv[a] != 0.0f ? mcx::recip_rn((double)q.u[a]) : 0.0;
       }
       q64.region = q.region;
       int k64 = 0;
@@ -264,7 +276,7 @@ __device__ __forceinline__ int box_collide(const BoxDev& b, mcs::Rng<M>& r, cons
   const double ug = r.next(l);
   uint32_t g2 = q.g;
   for (uint32_t k = q.g; k < b.ng; ++k) {
-    if (ug < b.cdf[rg][q.g][k]) {
+    if (mcs::nn_lt(ug, b.cdf[rg][q.g][k])) {  // both non-negative
       g2 = k;
       break;
     }

@@ -1,0 +1,140 @@
+// fp_exact.cuh -- fp64 results computed on the integer pipes, bit for bit
+// equal to the fp64 operations they replace.
+//
+// This GPU retires two fp64 lanes per clock per SM against 128 integer
+// lanes, and its fp64 unit spends the same time on a warp instruction
+// whatever the number of live lanes.  The fp64 transport kernels are bound by
+// that unit, so every fp64 step whose exact result can be assembled from
+// integer operations is moved off it:
+//   two_u_minus_1  2u - 1 for a draw u = n 2^-53 (exact: (2n - 2^53) 2^-53)
+//   floor_nonneg   floor(t) for 0 <= t < 2^63
+//   abs_le         |x| <= h for h >= 0
+//   recip_rn       1/y correctly rounded (IEEE round to nearest even)
+// All of them compile for host and device; the host copies let tests compare
+// them with the host's IEEE arithmetic.
+#pragma once
+#include <cstdint>
+
+#include "mc_log.cuh"  // to_bits, from_bits
+
+namespace mcx {
+
+using mclog::from_bits;
+using mclog::to_bits;
+
+__host__ __device__ __forceinline__ int clz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ float rcp_f32(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+
+// 2u - 1 for u = n 2^-53, 0 <= n < 2^53: the double (2n - 2^53) 2^-53,
+// exact (|2n - 2^53| <= 2^53), +0 for n = 2^52.
+__host__ __device__ __forceinline__ double two_u_minus_1(uint64_t n) {
+  const long long w = (long long)(n << 1) - (1ll << 53);
+  if (w == 0) return 0.0;
+  const uint64_t sign = w < 0 ? (1ull << 63) : 0ull;
+  const uint64_t a = w < 0 ? (uint64_t)(-w) : (uint64_t)w;  // 2 .. 2^53
+  if (a == (1ull << 53)) return -1.0;
+  const int lz = clz64(a);  // 11 .. 62
+  // leading 1 moved to bit 52; it carries into the exponent field, so the
+  // word to add is (biased exponent - 1) << 52 with biased = 1033 - lz
+  return from_bits(sign | ((a << (lz - 11)) + ((uint64_t)(1032 - lz) << 52)));
+}
+
+// floor(t) for 0 <= t < 2^63 (t finite, not negative zero excluded).
+__host__ __device__ __forceinline__ uint64_t floor_nonneg(double t) {
+  const uint64_t b = to_bits(t);
+  const int e = (int)(b >> 52) - 1023;
+  if (e < 0) return 0ull;
+  const uint64_t m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  return e <= 52 ? m >> (52 - e) : m << (e - 52);
+}
+
+// |x| <= h for h >= 0 (finite): non-negative doubles order like their bits.
+__host__ __device__ __forceinline__ bool abs_le(double x, double h) {
+  return (to_bits(x) & ~(1ull << 63)) <= to_bits(h);
+}
+
+// q = floor(2^105 / M) for 2^52 < M < 2^53, and the rounding of the exact
+// quotient to nearest (ties cannot occur: 2^106 = (2q + 1) M would make M a
+// power of two).  An fp32 reciprocal gives 22 bits; one Newton step on
+// 128-bit products and one on 64-bit remainders bring q within a few
+// units; an exact remainder fixes the last ones.
+__host__ __device__ __forceinline__ uint64_t recip_mantissa(uint64_t M) {
+  // 1. q0 ~ 2^105 / M from rf = RN(1 / (M >> 29)) ~ 2^29 / M
+  const uint32_t mh = (uint32_t)(M >> 29);  // [2^23, 2^24): exact in fp32
+  float rf = rcp_f32((float)mh);
+  uint32_t rb;
+#ifdef __CUDA_ARCH__
+  rb = __float_as_uint(rf);
+#else
+  std::memcpy(&rb, &rf, sizeof rb);
+#endif
+  const int er = (int)(rb >> 23) - 127;             // -24 or -23
+  const uint64_t mr = (uint64_t)((rb & 0x7FFFFFu) | 0x800000u);
+  uint64_t q = mr << (er + 53);                      // rf * 2^76, within 2^31 of 2^105 / M
+  // 2. e = 2^105 - q M on 128 bits; q += e q / 2^105 with e and q truncated
+  {
+    const uint64_t lo = q * M, hi = mulhi64(q, M);   // q M < 2^107
+    // e = (2^41 : 0) - (hi : lo)
+    const uint64_t elo = 0ull - lo;
+    const uint64_t ehi = (1ull << 41) - hi - (lo != 0ull ? 1ull : 0ull);
+    const long long es = (long long)((ehi << 12) | (elo >> 52));  // e >> 52, |es| < 2^32
+    const long long qs = (long long)(q >> 23);                      // < 2^31
+    const long long d = (es * qs) >> 30;                            // ~ e / M
+    q = (uint64_t)((long long)q + d);
+  }
+  // 3. e1 = 2^105 - q M fits in 64 signed bits now (|e1| < 2^62)
+  {
+    const long long e1 = (long long)(0ull - q * M);
+    const uint64_t ea = e1 < 0 ? (uint64_t)(-e1) : (uint64_t)e1;
+    const uint64_t d = mulhi64(ea, q) >> 41;  // ~ |e1| / M
+    q = e1 < 0 ? q - d : q + d;
+  }
+  // 4. exact remainder r = 2^105 - q M, 0 <= r < M, then round
+  long long r = (long long)(0ull - q * M);
+  for (int i = 0; i < 4 && r < 0; ++i) { --q; r += (long long)M; }
+  for (int i = 0; i < 4 && r >= (long long)M; ++i) { ++q; r -= (long long)M; }
+  if ((uint64_t)r * 2ull > M) ++q;
+  return q;
+}
+
+// RN(1 / y) on the integer pipes for normal y whose reciprocal is normal
+// (biased exponent 1..2044); the library division otherwise (zero,
+// subnormal, huge, inf, NaN).
+__host__ __device__ __forceinline__ double recip_rn(double y) {
+  const uint64_t b = to_bits(y);
+  const uint64_t sign = b & (1ull << 63);
+  const uint32_t E = (uint32_t)(b >> 52) & 0x7FFu;
+  if (E == 0u || E > 2044u) return 1.0 / y;
+  const uint64_t frac = b & ((1ull << 52) - 1ull);
+  if (frac == 0ull) return from_bits(sign | ((uint64_t)(2046u - E) << 52));  // a power of two
+  const uint64_t q = recip_mantissa(frac | (1ull << 52));  // in [2^52, 2^53)
+  return from_bits(sign | (((uint64_t)(2045u - E) << 52) + (q - (1ull << 52))));
+}
+
+// x 2^k for a normal x whose product stays normal (an exponent add).
+__host__ __device__ __forceinline__ double scale_pow2(double x, int k) {
+  return from_bits(to_bits(x) + ((uint64_t)(int64_t)k << 52));
+}
+
+}  // namespace mcx

@@ -139,6 +139,17 @@ __device__ __forceinline__ double u01_any(uint64_t x, uint32_t m) {
   return u53_to_double((uint32_t)(n >> 32), (uint32_t)n);
 }
 
+// The integer n of a draw's uniform u = n 2^-53 (0 <= n < 2^53): the top
+// 53 of the m state bits (m >= 53), or the state shifted up (m < 53).
+template <int M>
+__device__ __forceinline__ uint64_t u53(uint64_t x, uint32_t m) {
+  if constexpr (M == 63) {
+    return (x << 1) >> 11;
+  } else {
+    return m >= 53u ? (x & mask_of(m)) >> (m - 53u) : (x & mask_of(m)) << (53u - m);
+  }
+}
+
 template <int M>
 __device__ __forceinline__ double u01(uint64_t x, uint32_t m) {
   if constexpr (M == 63) {

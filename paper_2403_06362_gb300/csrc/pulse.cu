@@ -56,6 +56,19 @@ __global__ void pulse_prep_kernel(PulseDev* p) {
     p->inv_st = 1.0 / p->sigma_t;
     p->unit = __double2ll_rn(p->inv_st * mcs::kFix);
     p->seed_hash = mcd::seed_hash_of(p->seed);
+    p->c_n = (uint64_t)ceil(p->c * 0x1p53);
+    // floor(nu + u) over u = n 2^-53, n < 2^53, is floor(nu) or floor(nu) + 1
+    // (nu <= 64) and does not decrease with n: the first n giving the larger
+    // value, found with the same fp64 sum the transport definition uses
+    const double fl = floor(p->nu);
+    uint64_t lo = 0, hi = 1ull << 53;
+    while (lo < hi) {
+      const uint64_t mid = lo + ((hi - lo) >> 1);
+      if (floor(p->nu + (double)mid * 0x1p-53) > fl) hi = mid;
+      else lo = mid + 1;
+    }
+    p->nu_n = lo;
+    p->nu_floor = (uint32_t)fl;
   }
 }
 
@@ -128,7 +141,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
         r = mcs::Rng<M>{e.seed, 0ull};
         x = e.x;
         t = e.t;
-        mu = 2.0 * r.next(l) - 1.0;
+        mu = mcx::two_u_minus_1(r.next_n(l));
         events = 0;
         fam_draws = 0;
         sp = 0;
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
         r = mcs::Rng<M>{pulse_seed(P, gi, tab, l.mask), 0ull};
         x = 0.0;
         t = 0.0;
-        mu = 2.0 * r.next(l) - 1.0;
+        mu = mcx::two_u_minus_1(r.next_n(l));
         events = 0;
         fam_draws = 0;
         sp = 0;
@@ -164,22 +177,22 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
       ++lc.flights;
       const double d = -mclog::log1m(r.next(l)) * P.inv_st;
       const double tn = t + d;
-      if (tn >= P.t_end) {
+      if (!mcs::nn_lt(tn, P.t_end)) {  // tn >= t_end, both non-negative
         ++lc.census;
         ended = true;
       } else {
         const double xn = x + d * mu;
         ++lc.coll;
-        if (xn >= -P.x_half && xn <= P.x_half) {
-          uint32_t j = (uint32_t)floor(tn);
-          if (j >= P.n_time_bins) j = P.n_time_bins - 1;
+        if (mcx::abs_le(xn, P.x_half)) {
+          const uint64_t jf = mcx::floor_nonneg(tn);
+          const uint32_t j = jf < P.n_time_bins ? (uint32_t)jf : P.n_time_bins - 1;
           atomicAdd(row + j, (unsigned long long)P.unit);
         }
         x = xn;
         t = tn;
-        if (r.next(l) < P.c) {
+        if (r.next_n(l) < P.c_n) {  // u < c
           ++lc.scat;
-          const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
+          const uint32_t n = P.nu_floor + (r.next_n(l) >= P.nu_n ? 1u : 0u);  // floor(nu + u)
           for (uint32_t k = 0; k + 1 < n; ++k) {
             const uint64_t seed = hash_mode ? (mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask) : 0ull;
             if (sp < a.stack_depth) {
@@ -200,7 +213,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
               ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
             }
           }
-          mu = 2.0 * r.next(l) - 1.0;
+          mu = mcx::two_u_minus_1(r.next_n(l));
         } else {
           ++lc.absn;
           ended = true;
@@ -225,7 +238,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
       x = stack[sp].x;
       t = stack[sp].t;
       if (hash_mode) r = mcs::Rng<M>{stack[sp].seed, 0ull};
-      mu = 2.0 * r.next(l) - 1.0;
+      mu = mcx::two_u_minus_1(r.next_n(l));
       continue;
     }
     if (!hash_mode) {

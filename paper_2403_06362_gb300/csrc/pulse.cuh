@@ -18,6 +18,10 @@ struct PulseDev {
   double inv_st;
   long long unit;      // llrint(2^32 / Sigma_t): one collision-estimator score
   uint64_t seed_hash;  // flat hash mode: seed half of hash(., s)
+  // the draws' tests as integer thresholds on n (u = n 2^-53):
+  uint64_t c_n;        // u < c            <=>  n < c_n = ceil(c 2^53)
+  uint64_t nu_n;       // floor(nu + u) = nu_floor + (n >= nu_n)
+  uint32_t nu_floor, pad2;
 };
 
 constexpr int kStack = 256;

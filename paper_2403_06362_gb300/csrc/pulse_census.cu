@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           r = mcs::Rng<M>{e.seed, 0ull};
           x = e.x;
           t = e.t;
-          mu = 2.0 * r.next(l) - 1.0;
+          mu = mcx::two_u_minus_1(r.next_n(l));
           copies_left = 0;
           alive = true;
         } else if (a.in == nullptr) {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           r = mcs::Rng<M>{mcp::pulse_seed(P, g, nullptr, l.mask), 0ull};  // hash modes only
           x = 0.0;
           t = a.t0;
-          mu = 2.0 * r.next(l) - 1.0;
+          mu = mcx::two_u_minus_1(r.next_n(l));
           w = 1.0;
           unit_w = P.unit;
           wfix = (long long)mcs::kFix;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
       ++lc.flights;
       const double d = -mclog::log1m(r.next(l)) * P.inv_st;
       const double tn = t + d;
-      if (tn >= a.tp) {
+      if (!mcs::nn_lt(tn, a.tp)) {  // tn >= T_p, both non-negative
         ended = true;
         if (a.last) {
           ++lc.census;
@@ -265,16 +265,16 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
       } else {
         const double xn = x + d * mu;
         ++lc.coll;
-        if (xn >= -P.x_half && xn <= P.x_half) {
-          uint32_t j = (uint32_t)floor(tn);
-          if (j >= P.n_time_bins) j = P.n_time_bins - 1;
+        if (mcx::abs_le(xn, P.x_half)) {
+          const uint64_t jf = mcx::floor_nonneg(tn);
+          const uint32_t j = jf < P.n_time_bins ? (uint32_t)jf : P.n_time_bins - 1;
           atomicAdd(row + j, (unsigned long long)unit_w);
         }
         x = xn;
         t = tn;
-        if (r.next(l) < P.c) {
+        if (r.next_n(l) < P.c_n) {  // u < c
           ++lc.scat;
-          const uint32_t n = (uint32_t)floor(P.nu + r.next(l));
+          const uint32_t n = P.nu_floor + (r.next_n(l) >= P.nu_n ? 1u : 0u);  // floor(nu + u)
           for (uint32_t k = 0; k + 1 < n; ++k) {
             const uint64_t seed = mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask;
             if (sp < a.stack_depth) {
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
               }
             }
           }
-          mu = 2.0 * r.next(l) - 1.0;
+          mu = mcx::two_u_minus_1(r.next_n(l));
         } else {
           ++lc.absn;
           ended = true;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
       x = stack[sp].x;
       t = stack[sp].t;
       r = mcs::Rng<M>{stack[sp].seed, 0ull};
-      mu = 2.0 * r.next(l) - 1.0;
+      mu = mcx::two_u_minus_1(r.next_n(l));
       continue;
     }
     if (copies_left > 0) {  // next copy of the banked particle: Eq. (5) seed

@@ -34,6 +34,7 @@ __global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
     q.inv_h = (double)q.n_bins / q.L;
     q.inv_st = 1.0 / q.sigma_t;
     q.p_abs = 1.0 - q.c;
+    q.p_abs_n = (uint64_t)ceil(q.p_abs * 0x1p53);
     q.L_f = (float)q.L;
     q.h_f = q.L_f / (float)q.n_bins;
     q.inv_h_f = (float)q.n_bins / q.L_f;

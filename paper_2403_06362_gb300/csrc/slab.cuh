@@ -17,6 +17,7 @@
 
 #include "../../include/mc.h"
 #include "mc_device.cuh"
+#include "fp_exact.cuh"
 #include "mc_log.cuh"
 
 namespace mcs {
@@ -30,6 +31,7 @@ struct SlabDev {
   double inv_h;         // n_bins / L: candidate-bin lookup only
   double inv_st;        // 1 / sigma_t
   double p_abs;         // 1 - c
+  uint64_t p_abs_n;     // ceil((1 - c) 2^53): u < 1 - c  <=>  n < p_abs_n for u = n 2^-53
   float guard_f;        // fp32 path: half-width of the fp64 guard band at a face
   float L_f, h_f, inv_h_f, inv_st_f;
   uint64_t seed_hash;   // hash seeding: seed half of hash(., s) or of hash(., hash(key, s))
@@ -47,6 +49,13 @@ struct Rng {
     x = mcd::lcg_step(x, l.g, l.c);
     ++draws;
     return mcd::u01<M>(x, l.m);
+  }
+  // The same draw as its integer n (u = n 2^-53), for comparisons and exact
+  // integer arithmetic on u.
+  __device__ __forceinline__ uint64_t next_n(const mcd::Lcg& l) {
+    x = mcd::lcg_step(x, l.g, l.c);
+    ++draws;
+    return mcd::u53<M>(x, l.m);
   }
 };
 
@@ -182,7 +191,11 @@ struct SlabParticle {
   float xf, muf, wf;
 };
 
-__device__ __forceinline__ double fix_per_mu(double mu) { return mu != 0.0 ? __ddiv_rn(kFix, fabs(mu)) : 0.0; }
+// 2^32 / |mu| rounded once: 2^32 RN(1 / |mu|), the reciprocal on the
+// integer pipes (fp_exact.cuh), the scaling an exponent add.
+__device__ __forceinline__ double fix_per_mu(double mu) {
+  return mu != 0.0 ? mcx::scale_pow2(mcx::recip_rn(fabs(mu)), 32) : 0.0;
+}
 
 // Outcome of a flight or a collision.
 enum Outcome : int { kContinue = 0, kAbsorbed = 1, kLeakLo = 2, kLeakHi = 3, kCollide = 4 };
@@ -196,12 +209,12 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
     return;
   }
   const double u1 = r.next(l);
-  const double u2 = r.next(l);
   if constexpr (!F32) {
     q.x = __dmul_rn(p.L, u1);
-    q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
+    q.mu = mcx::two_u_minus_1(r.next_n(l));
     q.w_mu = fix_per_mu(q.mu);
   } else {
+    const double u2 = r.next(l);
     q.xf = p.L_f * (float)u1;
     q.muf = 2.0f * (float)u2 - 1.0f;
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
@@ -260,12 +273,12 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
 // scattering into a new direction (kContinue).
 template <int M, bool F32>
 __device__ __forceinline__ int slab_collide(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
-  if (nn_lt(r.next(l), p.p_abs)) return kAbsorbed;  // u < 1 - c, both non-negative
-  const double u2 = r.next(l);
+  if (r.next_n(l) < p.p_abs_n) return kAbsorbed;  // u < 1 - c
   if constexpr (!F32) {
-    q.mu = __dsub_rn(__dmul_rn(2.0, u2), 1.0);
+    q.mu = mcx::two_u_minus_1(r.next_n(l));
     q.w_mu = fix_per_mu(q.mu);
   } else {
+    const double u2 = r.next(l);
     q.muf = 2.0f * (float)u2 - 1.0f;
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
   }
