@@ -230,15 +230,15 @@ __device__ __forceinline__ void box_source(const BoxDev& b, mcs::Rng<M>& r, cons
 template <int M, typename T>
 __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q,
                                           unsigned long long* base) {
-  const double u = r.next(l);
   int kind = 0;
   T ds = surface<T>(b, q, kind);
   bool collide;
   T d;
   if constexpr (sizeof(T) == 8) {
-    d = -mclog::log1m(u) * b.inv_st[q.region];
+    d = -mclog::log1m_n(r.next_n(l)) * b.inv_st[q.region];
     collide = d < ds;
   } else {
+    const double u = r.next(l);
     d = -log1pf(-(float)u) * b.inv_st_f[q.region];
     collide = d < ds;
     if (fabsf(d - ds) <= 0x1p-16f * fmaxf(d, ds)) {  // near the surface: decide in fp64

@@ -1,19 +1,27 @@
-// mc_log.cuh -- ln(1 - u) for a uniform u in [0, 1): the logarithm of the
-// fp64 flight distance d = -ln(1 - u) / Sigma_t.
+// mc_log.cuh -- ln(1 - u) for a uniform u = n 2^-53 in [0, 1): the logarithm
+// of the fp64 flight distance d = -ln(1 - u) / Sigma_t, computed on the
+// integer pipes.
 //
-// Method: table-driven logarithm after P. T. P. Tang, "Table-driven
-// implementation of the logarithm function in IEEE floating-point
-// arithmetic", ACM TOMS 16(4), 1990.  With x = 1 - u = 2^k m, m in [1, 2), and
+// This GPU retires two fp64 lanes per clock per SM against 128 integer
+// lanes, so the logarithm is evaluated in fixed point with integer
+// operations and rounded once to the nearest double.  Method: the table
+// reduction of P. T. P. Tang, "Table-driven implementation of the logarithm
+// function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990.  With
+// x = 1 - u = K 2^-53 (K = 2^53 - n, exact) = 2^e m, m in [1, 2), and
 // F = 1 + (2j+1)/256 the midpoint of m's cell among 128 equal cells,
-//   ln x = k ln 2 + ln F + ln(1 + r),  r = (m - F) / F,  |r| < 2^-9,
-// where k ln2_hi + ln(F)_hi is exact (both parts are multiples of 2^-42) and
-// ln(1 + r) comes from its Taylor series through r^6.  For u < 2^-8, where x
-// is so close to 1 that k ln 2 + ln F would cancel, the Taylor series of
-// ln(1 - u) through u^8 is used instead.  The table path costs 14 fp64
-// operations (the library logarithm costs about 30 on this GPU, whose fp64
-// unit is narrow) and stays within about one ulp of the correctly rounded
-// value; tests compare it with the host C library.  The code is the same on
-// host and device (explicit fma, no contraction), so both give the same bits.
+//   ln x = e ln 2 + ln F + ln(1 + r),  r = (m - F) / F,  |r| < 2^-8,
+// where m - F is an exact integer difference, r is formed with a 64-bit
+// reciprocal of F (scale 2^71), ln(1 + r) comes from its series through r^8
+// by Horner's rule on 64-bit signed fixed point (scale 2^62), and the sum is
+// accumulated on 128 bits with scale 2^90 (ln 2 and ln F from 128-bit
+// tables).  For u < 2^-8 (x so close to 1 that e ln 2 + ln F would cancel)
+// -ln(1 - u) = u (1 + u/2 + ... + u^8/9) is used instead, relative to u.
+// The absolute error before the final rounding is below 2^-66 while the
+// result is at least 2^-8 in magnitude (relatively below 2^-60 in the
+// small-u branch), so the result is the correctly rounded logarithm except
+// within a few hundredths of an ulp of a rounding tie.  The code is plain
+// integer arithmetic, identical on host and device; tests compare it with a
+// 40-digit decimal logarithm and with the host C library.
 #pragma once
 #include <cmath>
 #include <cstdint>
@@ -23,15 +31,19 @@ namespace mclog {
 
 #define MC_LOG_CONST static constexpr
 #define MC_LOG_TABLE static __device__ const
+#define MC_LOG_COEF static __constant__ const
 namespace dev {
 #include "log_table.inc"
 }
 #undef MC_LOG_TABLE
+#undef MC_LOG_COEF
 #define MC_LOG_TABLE static const
+#define MC_LOG_COEF static const
 namespace host {
 #include "log_table.inc"
 }
 #undef MC_LOG_TABLE
+#undef MC_LOG_COEF
 #undef MC_LOG_CONST
 
 __host__ __device__ __forceinline__ uint64_t to_bits(double v) {
@@ -54,19 +66,81 @@ __host__ __device__ __forceinline__ double from_bits(uint64_t b) {
 #endif
 }
 
-// ln(1 - u) for 0 <= u < 1 with 1 - u exact (u a multiple of 2^-53, as every
-// uniform of the library is).
-__host__ __device__ __forceinline__ double log1m(double u) {
-  if (to_bits(u) < to_bits(0x1p-8)) {  // u < 2^-8 (u >= 0): -(u + u^2 q), q = 1/2 + u/3 + ... + u^6/8
-    double q = 1.0 / 8.0;
-    q = fma(q, u, 1.0 / 7.0);
-    q = fma(q, u, 1.0 / 6.0);
-    q = fma(q, u, 1.0 / 5.0);
-    q = fma(q, u, 1.0 / 4.0);
-    q = fma(q, u, 1.0 / 3.0);
-    q = fma(q, u, 1.0 / 2.0);
-    return 0.0 - fma(u, u * q, u);  // u^2 q < u 2^-9: one rounding of the sum dominates; +0 at u = 0
+__host__ __device__ __forceinline__ int clz64_(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)x);
+#else
+  return x ? __builtin_clzll(x) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint64_t umulhi_(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ long long smulhi_(long long a, long long b) {
+#ifdef __CUDA_ARCH__
+  return __mul64hi(a, b);
+#else
+  return (long long)(((__int128)a * b) >> 64);
+#endif
+}
+
+// A 128-bit two's-complement integer.
+struct W128 {
+  uint64_t lo, hi;
+};
+
+__host__ __device__ __forceinline__ W128 add128(W128 a, W128 b) {
+  W128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+
+__host__ __device__ __forceinline__ W128 neg128(W128 a) {
+  W128 r;
+  r.lo = 0ull - a.lo;
+  r.hi = ~a.hi + (a.lo == 0ull ? 1ull : 0ull);
+  return r;
+}
+
+// a 2^-scale as the nearest double (round half to even), a > 0, the result
+// normal.
+__host__ __device__ __forceinline__ double w128_to_double(W128 a, int scale) {
+  const int lz = a.hi ? clz64_(a.hi) : 64 + clz64_(a.lo);
+  const int top = 127 - lz;  // position of the leading 1
+  uint64_t m64;              // the leading 64 bits, leading 1 at bit 63
+  bool sticky;
+  if (top >= 63) {
+    const int sh = top - 63;  // 0..64
+    if (sh == 0) {
+      m64 = a.lo;
+      sticky = false;
+    } else if (sh < 64) {
+      m64 = (a.hi << (64 - sh)) | (a.lo >> sh);
+      sticky = (a.lo << (64 - sh)) != 0ull;
+    } else {
+      m64 = a.hi;
+      sticky = a.lo != 0ull;
+    }
+  } else {
+    m64 = a.lo << (63 - top);
+    sticky = false;
   }
+  uint64_t m53 = m64 >> 11;
+  const uint64_t rest = m64 & 0x7FFull;
+  if (rest > 0x400ull || (rest == 0x400ull && (sticky || (m53 & 1ull)))) ++m53;  // may carry to 2^53
+  const uint64_t biased = (uint64_t)(top - scale + 1023);
+  return from_bits(((biased - 1ull) << 52) + m53);  // the leading 1 adds one to the exponent
+}
+
+// ln(1 - u) for u = n 2^-53, 0 <= n < 2^53: a double <= 0 (+0 for n = 0).
+__host__ __device__ __forceinline__ double log1m_n(uint64_t n) {
 #ifdef __CUDA_ARCH__
   using namespace dev;
 #define MC_LOG_LD(a, i) __ldg(&(a)[(i)])
@@ -74,25 +148,59 @@ __host__ __device__ __forceinline__ double log1m(double u) {
   using namespace host;
 #define MC_LOG_LD(a, i) (a)[(i)]
 #endif
-  const double x = 1.0 - u;  // exact, in [2^-53, 1 - 2^-8]
-  const uint64_t bits = to_bits(x);
-  const int k = (int)(bits >> 52) - 1023;
-  const uint64_t mant = bits & ((1ull << 52) - 1ull);
-  const int j = (int)(mant >> 45);
-  const double m = from_bits(0x3FF0000000000000ull | mant);
-  const double F = from_bits(0x3FF0000000000000ull | ((uint64_t)(2 * j + 1) << 44));
-  const double r = (m - F) * MC_LOG_LD(kInvF, j);  // m - F exact (Sterbenz)
-  double q = -1.0 / 6.0;
-  q = fma(q, r, 1.0 / 5.0);
-  q = fma(q, r, -1.0 / 4.0);
-  q = fma(q, r, 1.0 / 3.0);
-  q = fma(q, r, -1.0 / 2.0);
-  const double p = fma(r * r, q, r);  // ln(1 + r)
-  const double kd = (double)k;
-  const double s = fma(kd, kLn2Hi, MC_LOG_LD(kLnFHi, j));  // exact
-  const double t = fma(kd, kLn2Lo, MC_LOG_LD(kLnFLo, j)) + p;
+  if (n < (1ull << 45)) {  // u < 2^-8: -u (1 + u/2 + ... + u^8/9)
+    if (n == 0ull) return 0.0;
+    const long long U = (long long)(n << 18);  // u 2^71
+    long long t = kLn1mB[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) t = kLn1mB[k] + (smulhi_(U, t) >> 7);  // scale 2^62
+    W128 p;
+    p.lo = n * (uint64_t)t;
+    p.hi = umulhi_(n, (uint64_t)t);  // n t = -ln(1 - u) 2^115
+    return -w128_to_double(p, 115);
+  }
+  const uint64_t K = (1ull << 53) - n;  // x = K 2^-53, 1 <= K < 2^53 - 2^45
+  const int lz = clz64_(K);             // 12..63
+  const int e = 10 - lz;                // x = 2^e m
+  const uint64_t mant = K << (lz - 11);  // m 2^52, leading 1 at bit 52
+  const int j = (int)((mant >> 45) & 127ull);
+  const long long D = (long long)mant - (long long)((1ull << 52) + ((uint64_t)(2 * j + 1) << 44));  // (m - F) 2^52
+  const uint64_t inv = MC_LOG_LD(kInvF, j);                                                        // 2^64 / F
+  const uint64_t ad = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
+  const uint64_t pr = (umulhi_(ad, inv) << 19) | ((ad * inv) >> 45);  // |r| 2^71
+  const long long R = D < 0 ? -(long long)pr : (long long)pr;
+  long long t = kLn1pC[7];
+#pragma unroll
+  for (int k = 6; k >= 0; --k) t = kLn1pC[k] + (smulhi_(R, t) >> 7);  // scale 2^62
+  // ln(1 + r) 2^71 = (R t) >> 62, then to scale 2^90
+  const long long ph = smulhi_(R, t);
+  const uint64_t pl = (uint64_t)R * (uint64_t)t;
+  const long long p71 = (long long)(((uint64_t)ph << 2) | (pl >> 62));
+  W128 s;
+  s.lo = (uint64_t)p71 << 19;
+  s.hi = (uint64_t)(p71 >> 45);
+  // + ln F
+  W128 f;
+  f.lo = MC_LOG_LD(kLnFLo, j);
+  f.hi = MC_LOG_LD(kLnFHi, j);
+  s = add128(s, f);
+  // + e ln 2 (e < 0)
+  const uint64_t ae = (uint64_t)(-e);
+  W128 l2;
+  l2.lo = ae * kLn2Lo;
+  l2.hi = umulhi_(ae, kLn2Lo) + ae * kLn2Hi;
+  s = add128(s, neg128(l2));
 #undef MC_LOG_LD
-  return s + t;
+  return -w128_to_double(neg128(s), 90);  // s < 0
+}
+
+// ln(1 - u) for a double u = n 2^-53 in [0, 1) (every uniform of the library).
+__host__ __device__ __forceinline__ double log1m(double u) {
+  const uint64_t b = to_bits(u);
+  if (b == 0ull) return 0.0;
+  const int e = (int)(b >> 52) - 1023;  // u = (1.f) 2^e, e in [-53, -1]
+  const uint64_t m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  return log1m_n(m >> (-e - 1));  // n = u 2^53 = m 2^(e + 1)
 }
 
 }  // namespace mclog

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
     } else {
       ++events;
       ++lc.flights;
-      const double d = -mclog::log1m(r.next(l)) * P.inv_st;
+      const double d = -mclog::log1m_n(r.next_n(l)) * P.inv_st;
       const double tn = t + d;
       if (!mcs::nn_lt(tn, P.t_end)) {  // tn >= t_end, both non-negative
         ++lc.census;

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
     } else {
       ++events;
       ++lc.flights;
-      const double d = -mclog::log1m(r.next(l)) * P.inv_st;
+      const double d = -mclog::log1m_n(r.next_n(l)) * P.inv_st;
       const double tn = t + d;
       if (!mcs::nn_lt(tn, a.tp)) {  // tn >= T_p, both non-negative
         ended = true;

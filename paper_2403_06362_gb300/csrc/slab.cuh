@@ -226,9 +226,8 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
 template <int M, bool F32>
 __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q,
                                            const Sink& s) {
-  const double u = r.next(l);
   if constexpr (!F32) {
-    const double d = __dmul_rn(-mclog::log1m(u), p.inv_st);
+    const double d = __dmul_rn(-mclog::log1m_n(r.next_n(l)), p.inv_st);
     const double xn = __dadd_rn(q.x, __dmul_rn(d, q.mu));
     // mu is never -0 (2u - 1 rounds an exact zero to +0), so its sign is the
     // sign of its bit pattern; x, L and the positions of a forward flight are
@@ -241,6 +240,7 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
     else seg64(p, xn, q.x, q.w_mu, s);
     q.x = xn;
   } else {
+    const double u = r.next(l);
     const float d = -log1pf(-(float)u) * p.inv_st_f;
     float xn = fmaf(d, q.muf, q.xf);
     // Guard band: re-decide leak vs collide in fp64 near a face.
