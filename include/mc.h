@@ -342,6 +342,11 @@ MC_API int mc_log1m_device(const double* d_u, double* d_out, uint64_t n, int whi
  * MC_ERR_CUDA. */
 MC_API double mc_recip_rn(double y);
 MC_API double mc_two_u_minus_1(uint64_t n);
+/* llrint(v) for 0 <= v < 2^62; a < b for non-NaN doubles (1 or 0); RN(j h)
+ * for 0 <= j < 2^11 and a normal h > 0 with a normal product. */
+MC_API long long mc_llrint_nonneg(double v);
+MC_API int mc_d_lt(double a, double b);
+MC_API double mc_mul_small(uint32_t j, double h);
 MC_API int mc_recip_rn_device(const double* d_y, double* d_out, uint64_t n, int which, void* stream);
 
 /* Section 5 normality procedure on host data x[n_batches][n_points]: the

@@ -116,6 +116,11 @@ def mc_two_u_minus_1(n: int) -> float:
     return float(lib().mc_two_u_minus_1(int(n)))
 
 
+def mc_mul_small(j: int, h: float) -> float:
+    """RN(j h) for a small integer j, assembled from integer operations (host evaluation)."""
+    return float(lib().mc_mul_small(int(j), float(h)))
+
+
 def mc_recip_rn_device(d_y, d_out, which=0, stream=None):
     """d_out = 1/d_y on the device: which 0 = the integer-pipe reciprocal,
     1 = the CUDA division (fp64 tensors of equal length)."""

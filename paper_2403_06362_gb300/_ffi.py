@@ -33,7 +33,7 @@ EXPORTED = [
     "mc_last_error", "mc_ctx_create", "mc_ctx_destroy", "mc_seed_hash", "mc_seed_stride",
     "mc_lcg_draw", "mc_transport_run", "mc_tally_read", "mc_hash64", "mc_normality",
     "mc_transport_run_static", "mc_autotune", "mc_log1m", "mc_log1m_device", "mc_recip_rn",
-    "mc_two_u_minus_1", "mc_recip_rn_device",
+    "mc_two_u_minus_1", "mc_recip_rn_device", "mc_llrint_nonneg", "mc_d_lt", "mc_mul_small",
 ]
 
 
@@ -127,6 +127,9 @@ def _load():
         "mc_recip_rn": (dbl, [dbl]),
         "mc_two_u_minus_1": (dbl, [u64]),
         "mc_recip_rn_device": (i32, [P, P, u64, i32, P]),
+        "mc_llrint_nonneg": (C.c_longlong, [dbl]),
+        "mc_d_lt": (i32, [dbl, dbl]),
+        "mc_mul_small": (dbl, [u32, dbl]),
         "mc_autotune": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_problem), u32, C.POINTER(mc_run_config),
                               C.POINTER(mc_tally), C.POINTER(mc_run_config), C.POINTER(C.c_float), P]),
         "mc_transport_run_static": (i32, [C.POINTER(mc_lcg), C.POINTER(mc_problem), u32,

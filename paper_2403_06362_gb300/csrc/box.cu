@@ -28,6 +28,7 @@ __global__ void box_prep_kernel(BoxDev* __restrict__ p, uint32_t n) {
     BoxDev& b = p[i];
     b.h = b.side / (double)b.mesh;
     b.inv_h = (double)b.mesh / b.side;
+    mcx::fixed_of(b.inv_h, b.ih_q, b.ih_s);
     b.side_f = (float)b.side;
     b.lo_f = (float)b.lo;
     b.hi_f = (float)b.hi;

@@ -34,6 +34,8 @@ struct BoxDev {
   uint32_t ng, mesh, max_split, n_batches, seeding, source;
   // derived on the device (box_prep_kernel)
   double inv_st[2], h, inv_h;
+  uint32_t ih_q;  // inv_h as ih_q 2^-ih_s: the voxel lookup guess
+  int ih_s;
   float side_f, lo_f, hi_f, h_f, inv_h_f;
   float inv_st_f[2], c_f[2], wl_f[2], wh_f[2], ws_f[2];
   uint64_t seed_hash, hist_begin;
@@ -67,6 +69,19 @@ template <typename T> __device__ __forceinline__ T sel(const double& d, const fl
 template <> __device__ __forceinline__ double sel<double>(const double& d, const float&) { return d; }
 template <> __device__ __forceinline__ float sel<float>(const double&, const float& f) { return f; }
 
+// Comparisons: fp64 on the integer pipes (sign-magnitude order keys, equal to
+// the fp64 comparisons for non-NaN values), fp32 native.
+__device__ __forceinline__ bool lt(double a, double b) { return mcx::d_lt(a, b); }
+__device__ __forceinline__ bool lt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool eq(double a, double b) { return mcx::okey(a) == mcx::okey(b); }
+__device__ __forceinline__ bool eq(float a, float b) { return a == b; }
+__device__ __forceinline__ bool gt0(double a) { return mcx::d_pos(a); }
+__device__ __forceinline__ bool gt0(float a) { return a > 0.0f; }
+__device__ __forceinline__ bool lt0(double a) { return mcx::d_neg(a); }
+__device__ __forceinline__ bool lt0(float a) { return a < 0.0f; }
+__device__ __forceinline__ bool is0(double a) { return mcx::d_zero(a); }
+__device__ __forceinline__ bool is0(float a) { return a == 0.0f; }
+
 template <typename T> __device__ __forceinline__ T recip(T v);
 template <> __device__ __forceinline__ double recip<double>(double v) { return mcx::recip_rn(v); }
 template <> __device__ __forceinline__ float recip<float>(float v) { return 1.0f / v; }
@@ -76,7 +91,7 @@ template <> __device__ __forceinline__ float recip<float>(float v) { return 1.0f
 template <typename T>
 __device__ __forceinline__ void set_inv(Part<T>& q) {
 #pragma unroll 1
-  for (int a = 0; a < 3; ++a) q.inv[a] = q.u[a] != T(0) ? recip<T>(q.u[a]) : T(0);
+  for (int a = 0; a < 3; ++a) q.inv[a] = !is0(q.u[a]) ? recip<T>(q.u[a]) : T(0);
 }
 
 // Marsaglia (1972): v1, v2 uniform on [-1,1)^2 until v1^2 + v2^2 < 1.
@@ -92,7 +107,7 @@ __device__ __forceinline__ void iso_dir(mcs::Rng<M>& r, const mcd::Lcg& l, T u[3
       v2 = T(2) * from_u<T>(r.next(l)) - T(1);
     }
     s = v1 * v1 + v2 * v2;
-  } while (s >= T(1));
+  } while (!lt(s, T(1)));
   const T t = sqrt(T(1) - s);
   u[0] = T(2) * v1 * t;
   u[1] = T(2) * v2 * t;
@@ -103,8 +118,8 @@ template <typename T>
 __device__ __forceinline__ uint32_t region_of(const BoxDev& b, const T p[3], const T u[3]) {
   const T lo = sel<T>(b.lo, b.lo_f), hi = sel<T>(b.hi, b.hi_f);
   for (int a = 0; a < 3; ++a) {
-    const bool above = p[a] > lo || (p[a] == lo && u[a] > T(0));
-    const bool below = p[a] < hi || (p[a] == hi && u[a] < T(0));
+    const bool above = lt(lo, p[a]) || (eq(p[a], lo) && gt0(u[a]));
+    const bool below = lt(p[a], hi) || (eq(p[a], hi) && lt0(u[a]));
     if (!above || !below) return 0u;
   }
   return 1u;
@@ -115,28 +130,29 @@ __device__ __forceinline__ T exit_dist(const Part<T>& q, T lo, T hi) {
   T t = T(INFINITY);
   for (int a = 0; a < 3; ++a) {
     T ta;
-    if (q.u[a] > T(0)) ta = (hi - q.p[a]) * q.inv[a];
-    else if (q.u[a] < T(0)) ta = (lo - q.p[a]) * q.inv[a];
+    if (gt0(q.u[a])) ta = (hi - q.p[a]) * q.inv[a];
+    else if (lt0(q.u[a])) ta = (lo - q.p[a]) * q.inv[a];
     else continue;
-    if (ta < t) t = ta;
+    if (lt(ta, t)) t = ta;
   }
-  return t < T(0) ? T(0) : t;
+  return lt0(t) ? T(0) : t;
 }
 
 template <typename T>
 __device__ __forceinline__ T entry_dist(const Part<T>& q, T lo, T hi) {
   T tn = T(-INFINITY), tf = T(INFINITY);
   for (int a = 0; a < 3; ++a) {
-    if (q.u[a] != T(0)) {
+    if (!is0(q.u[a])) {
       const T t1 = (lo - q.p[a]) * q.inv[a], t2 = (hi - q.p[a]) * q.inv[a];
-      const T tmin = t1 < t2 ? t1 : t2, tmax = t1 < t2 ? t2 : t1;
-      if (tmin > tn) tn = tmin;
-      if (tmax < tf) tf = tmax;
-    } else if (q.p[a] <= lo || q.p[a] >= hi) {
+      const bool o = lt(t1, t2);
+      const T tmin = o ? t1 : t2, tmax = o ? t2 : t1;
+      if (lt(tn, tmin)) tn = tmin;
+      if (lt(tmax, tf)) tf = tmax;
+    } else if (!lt(lo, q.p[a]) || !lt(q.p[a], hi)) {
       return T(INFINITY);
     }
   }
-  if (tn >= T(0) && tn < tf) return tn;
+  if (!lt0(tn) && lt(tn, tf)) return tn;
   return T(INFINITY);
 }
 
@@ -151,16 +167,28 @@ __device__ __forceinline__ T surface(const BoxDev& b, const Part<T>& q, int& kin
   }
   const T de = entry_dist(q, lo, hi);
   const T dx = exit_dist(q, T(0), side);
-  kind = de < dx ? 1 : 2;
-  return de < dx ? de : dx;
+  const bool in = lt(de, dx);
+  kind = in ? 1 : 2;
+  return in ? de : dx;
 }
 
-__device__ __forceinline__ long long fix_of(double wl) { return __double2ll_rn(wl * mcs::kFix); }
+__device__ __forceinline__ long long fix_of(double wl) { return mcx::fix32_nonneg(wl); }
 __device__ __forceinline__ long long fix_of(float wl) { return mcs::fix32_from_float(wl); }
 
-template <typename T>
-__device__ __forceinline__ T plane(const BoxDev& b, int j) {
-  return j >= (int)b.mesh ? sel<T>(b.side, b.side_f) : (T)j * sel<T>(b.h, b.h_f);
+template <typename T> __device__ __forceinline__ T plane(const BoxDev& b, int j);
+template <> __device__ __forceinline__ double plane<double>(const BoxDev& b, int j) {
+  return j >= (int)b.mesh ? b.side : mcx::mul_small((uint32_t)j, b.h);  // RN(j h), mesh <= 1024
+}
+template <> __device__ __forceinline__ float plane<float>(const BoxDev& b, int j) {
+  return j >= (int)b.mesh ? b.side_f : (float)j * b.h_f;
+}
+
+template <typename T> __device__ __forceinline__ int voxel_guess(const BoxDev& b, T p);
+template <> __device__ __forceinline__ int voxel_guess<double>(const BoxDev& b, double p) {
+  return lt0(p) ? -1 : (int)min(mcx::guess_floor_mul(p, b.ih_q, b.ih_s), (uint64_t)b.mesh);
+}
+template <> __device__ __forceinline__ int voxel_guess<float>(const BoxDev& b, float p) {
+  return (int)floorf(p * b.inv_h_f);
 }
 
 // Track-length tally of p + t u, 0 <= t <= L, by a voxel walk: the next
@@ -174,25 +202,27 @@ __device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long
   int idx[3];
   T tn[3];
   for (int a = 0; a < 3; ++a) {
-    int i = (int)floor(q.p[a] * inv_h);
+    int i = voxel_guess<T>(b, q.p[a]);
     i = i < 0 ? 0 : (i >= nm ? nm - 1 : i);
-    while (i > 0 && q.p[a] < plane<T>(b, i)) --i;
-    while (i + 1 < nm && q.p[a] >= plane<T>(b, i + 1)) ++i;
-    if (q.u[a] < T(0) && i > 0 && q.p[a] == plane<T>(b, i)) --i;
+    while (i > 0 && lt(q.p[a], plane<T>(b, i))) --i;
+    while (i + 1 < nm && !lt(q.p[a], plane<T>(b, i + 1))) ++i;
+    if (lt0(q.u[a]) && i > 0 && eq(q.p[a], plane<T>(b, i))) --i;
     idx[a] = i;
-    if (q.u[a] > T(0)) tn[a] = (plane<T>(b, i + 1) - q.p[a]) * q.inv[a];
-    else if (q.u[a] < T(0)) tn[a] = (plane<T>(b, i) - q.p[a]) * q.inv[a];
+    if (gt0(q.u[a])) tn[a] = (plane<T>(b, i + 1) - q.p[a]) * q.inv[a];
+    else if (lt0(q.u[a])) tn[a] = (plane<T>(b, i) - q.p[a]) * q.inv[a];
     else tn[a] = T(INFINITY);
   }
   (void)h;
+  (void)inv_h;
   T t = T(0);
   const T w = q.w;
   for (int guard = 0; guard < 3 * nm + 8; ++guard) {
     int a = 0;
-    if (tn[1] < tn[a]) a = 1;
-    if (tn[2] < tn[a]) a = 2;
-    const T tend = tn[a] < L ? tn[a] : L;
-    if (tend > t) {
+    if (lt(tn[1], tn[a])) a = 1;
+    if (lt(tn[2], tn[a])) a = 2;
+    const bool inside = lt(tn[a], L);
+    const T tend = inside ? tn[a] : L;
+    if (lt(t, tend)) {
       const long long v = fix_of(w * (tend - t));
       if (v != 0) {
         const uint64_t slot = ((uint64_t)idx[2] * nm + idx[1]) * nm + idx[0];
@@ -200,9 +230,9 @@ __device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long
       }
       t = tend;
     }
-    if (!(tn[a] < L)) break;
+    if (!inside) break;
     // step across the plane on axis a
-    if (q.u[a] > T(0)) {
+    if (gt0(q.u[a])) {
       idx[a] += 1;
       if (idx[a] >= nm) break;
       tn[a] = (plane<T>(b, idx[a] + 1) - q.p[a]) * q.inv[a];
@@ -236,7 +266,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
   T d;
   if constexpr (sizeof(T) == 8) {
     d = -mclog::log1m_n(r.next_n(l)) * b.inv_st[q.region];
-    collide = d < ds;
+    collide = lt(d, ds);
   } else {
     const double u = r.next(l);
     d = -log1pf(-(float)u) * b.inv_st_f[q.region];
@@ -285,15 +315,15 @@ __device__ __forceinline__ int box_collide(const BoxDev& b, mcs::Rng<M>& r, cons
   iso_dir<M, T>(r, l, q.u);
   set_inv(q);
   const T wl = sel<T>(b.wl[rg], b.wl_f[rg]), wh = sel<T>(b.wh[rg], b.wh_f[rg]);
-  if (q.w < wl) {
+  if (lt(q.w, wl)) {
     const T ws = sel<T>(b.ws[rg], b.ws_f[rg]);
-    if (from_u<T>(r.next(l)) < q.w / ws) {
+    if (lt(from_u<T>(r.next(l)), q.w / ws)) {
       q.w = ws;
       return kBoxContinue;
     }
     return kBoxKilled;
   }
-  if (q.w > wh) {
+  if (lt(wh, q.w)) {
     const T nd = ceil(q.w / wh);
     const uint32_t ns = nd > (T)b.max_split ? b.max_split : (uint32_t)nd;
     if (ns > 1u) {

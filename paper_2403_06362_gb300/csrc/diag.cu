@@ -32,6 +32,12 @@ MC_API double mc_recip_rn(double y) { return mcx::recip_rn(y); }
 
 MC_API double mc_two_u_minus_1(uint64_t n) { return n < (1ull << 53) ? mcx::two_u_minus_1(n) : 0.0; }
 
+MC_API long long mc_llrint_nonneg(double v) { return mcx::llrint_nonneg(v); }
+
+MC_API int mc_d_lt(double a, double b) { return mcx::d_lt(a, b) ? 1 : 0; }
+
+MC_API double mc_mul_small(uint32_t j, double h) { return mcx::mul_small(j, h); }
+
 MC_API int mc_recip_rn_device(const double* d_y, double* d_out, uint64_t n, int which, void* stream) {
   if ((n && (!d_y || !d_out)) || (which != 0 && which != 1)) {
     mci::set_error("mc_recip_rn_device: NULL buffer or which not in {0, 1}");

@@ -10,6 +10,9 @@
 //   floor_nonneg   floor(t) for 0 <= t < 2^63
 //   abs_le         |x| <= h for h >= 0
 //   recip_rn       1/y correctly rounded (IEEE round to nearest even)
+//   llrint_nonneg  llrint(v) for 0 <= v < 2^62
+//   okey, d_lt ..  comparisons of doubles (sign-magnitude order keys)
+//   mul_small      RN(j h) for a small integer j
 // All of them compile for host and device; the host copies let tests compare
 // them with the host's IEEE arithmetic.
 #pragma once
@@ -130,6 +133,75 @@ __host__ __device__ __forceinline__ double recip_rn(double y) {
   if (frac == 0ull) return from_bits(sign | ((uint64_t)(2046u - E) << 52));  // a power of two
   const uint64_t q = recip_mantissa(frac | (1ull << 52));  // in [2^52, 2^53)
   return from_bits(sign | (((uint64_t)(2045u - E) << 52) + (q - (1ull << 52))));
+}
+
+// llrint(v) (round half to even) for 0 <= v < 2^62, from the bits.
+__host__ __device__ __forceinline__ long long llrint_nonneg(double v) {
+  const uint64_t b = to_bits(v);
+  const int e = (int)(b >> 52) - 1023;
+  if (e < -1) return 0;  // v < 1/2
+  const uint64_t m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  if (e >= 52) return (long long)(m << (e - 52));
+  const int sh = 52 - e;  // 1..53
+  const uint64_t q = m >> sh, rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  return (long long)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+}
+
+// Order key of a non-NaN double: a < b  <=>  okey(a) < okey(b); -0 and +0
+// share the key 0.
+__host__ __device__ __forceinline__ long long okey(double x) {
+  const uint64_t b = to_bits(x);
+  const long long m = (long long)(b & ~(1ull << 63));
+  return (b >> 63) ? -m : m;
+}
+__host__ __device__ __forceinline__ bool d_lt(double a, double b) { return okey(a) < okey(b); }
+__host__ __device__ __forceinline__ bool d_pos(double a) { return (long long)to_bits(a) > 0; }        // a > 0
+__host__ __device__ __forceinline__ bool d_neg(double a) { return to_bits(a) > (1ull << 63); }         // a < 0
+__host__ __device__ __forceinline__ bool d_zero(double a) { return (to_bits(a) << 1) == 0ull; }        // a == 0
+
+// RN(j h) for an integer 0 <= j < 2^11 and a normal h > 0 whose product
+// stays normal: the exact product m_h j has at most 64 bits, rounded once.
+__host__ __device__ __forceinline__ double mul_small(uint32_t j, double h) {
+  if (j == 0u) return 0.0;
+  const uint64_t b = to_bits(h);
+  const uint64_t m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+  const uint64_t p = m * (uint64_t)j;  // < 2^64
+  const int lz = clz64(p);             // 0..11
+  const int sh = 11 - lz;              // bits below the 53 kept
+  uint64_t q = p >> sh;
+  if (sh > 0) {
+    const uint64_t rem = p & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (q & 1ull))) ++q;  // may carry to 2^53
+  }
+  // value = q 2^(E_h + sh - 1075): biased exponent E_h + sh with q's leading
+  // 1 at bit 52 (a carry to 2^53 moves into the exponent by itself)
+  return from_bits((b & ~((1ull << 52) - 1ull)) + ((uint64_t)sh << 52) + (q - (1ull << 52)));
+}
+
+// A positive normal x as q 2^-s with a 32-bit q in [2^31, 2^32) (truncated),
+// and floor(a x) within one for 0 <= a from it: a lookup guess that an exact
+// comparison then corrects.
+__host__ __device__ __forceinline__ void fixed_of(double x, uint32_t& q, int& s) {
+  const uint64_t b = to_bits(x);
+  q = (uint32_t)((((b & ((1ull << 52) - 1ull)) | (1ull << 52))) >> 21);
+  s = 31 - ((int)(b >> 52) - 1023);
+}
+__host__ __device__ __forceinline__ uint64_t guess_floor_mul(double a, uint32_t q, int s) {
+  const uint64_t b = to_bits(a);
+  if ((b << 1) == 0ull) return 0ull;
+  const int e = (int)(b >> 52) - 1023;
+  const uint64_t m32 = (((b & ((1ull << 52) - 1ull)) | (1ull << 52))) >> 21;  // a ~ m32 2^(e - 31)
+  const int sh = 31 + s - e;
+  if (sh >= 64) return 0ull;
+  if (sh <= 0) return 1ull << 40;
+  return (m32 * (uint64_t)q) >> sh;
+}
+
+// llrint(w 2^32) for w >= 0 (2^32 w < 2^62): the scaling as an exponent add.
+__host__ __device__ __forceinline__ long long fix32_nonneg(double w) {
+  const uint64_t b = to_bits(w);
+  if ((b >> 52) == 0ull) return 0;  // zero or below 2^-1022
+  return llrint_nonneg(from_bits(b + (32ull << 52)));
 }
 
 // x 2^k for a normal x whose product stays normal (an exponent add).

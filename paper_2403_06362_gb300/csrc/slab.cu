@@ -32,6 +32,7 @@ __global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
     SlabDev& q = p[i];
     q.h = q.L / (double)q.n_bins;
     q.inv_h = (double)q.n_bins / q.L;
+    mcx::fixed_of(q.inv_h, q.ih_q, q.ih_s);
     q.inv_st = 1.0 / q.sigma_t;
     q.p_abs = 1.0 - q.c;
     q.p_abs_n = (uint64_t)ceil(q.p_abs * 0x1p53);

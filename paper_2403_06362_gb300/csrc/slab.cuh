@@ -29,6 +29,8 @@ struct SlabDev {
   // derived on the device by the prep kernel
   double h;             // bin width L / n_bins
   double inv_h;         // n_bins / L: candidate-bin lookup only
+  uint32_t ih_q;        // inv_h as ih_q 2^-ih_s (the lookup on the integer pipes)
+  int ih_s;
   double inv_st;        // 1 / sigma_t
   double p_abs;         // 1 - c
   uint64_t p_abs_n;     // ceil((1 - c) 2^53): u < 1 - c  <=>  n < p_abs_n for u = n 2^-53
@@ -85,7 +87,13 @@ __device__ __forceinline__ uint64_t batch_of(uint64_t id, uint64_t n_hist, uint3
 }
 
 __device__ __forceinline__ double slab_edge(const SlabDev& p, int j) {
-  return j >= (int)p.n_bins ? p.L : (double)j * p.h;
+  if (j >= (int)p.n_bins) return p.L;
+  return j < 2048 ? mcx::mul_small((uint32_t)j, p.h) : (double)j * p.h;  // RN(j h)
+}
+
+// A bin index within one of floor(x n_bins / L), x >= 0 (integer pipes).
+__device__ __forceinline__ int bin_guess(const SlabDev& p, double x) {
+  return (int)min(mcx::guess_floor_mul(x, p.ih_q, p.ih_s), (uint64_t)p.n_bins);
 }
 
 __device__ __forceinline__ int clamp_bin(int j, int nb) { return j < 0 ? 0 : (j >= nb ? nb - 1 : j); }
@@ -120,7 +128,7 @@ __device__ __forceinline__ double edge_of(const SlabDev& p, const Sink& s, int j
 // overlaps, starting from the one that holds a.
 __device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, double w_fix, const Sink& s) {
   const int nb = (int)p.n_bins;
-  int j = clamp_bin((int)(a * p.inv_h), nb);
+  int j = clamp_bin(bin_guess(p, a), nb);
   while (j > 0 && nn_lt(a, edge_of(p, s, j))) --j;
   while (j + 1 < nb && !nn_lt(a, edge_of(p, s, j + 1))) ++j;
   double lo = a;
@@ -137,10 +145,10 @@ __device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, doub
 // mu == 0: the whole flight d lies in the bin holding x.
 __device__ __forceinline__ void point64(const SlabDev& p, double x, double d, const Sink& s) {
   const int nb = (int)p.n_bins;
-  int j = clamp_bin((int)(x * p.inv_h), nb);
-  while (j > 0 && x < slab_edge(p, j)) --j;
-  while (j + 1 < nb && x >= slab_edge(p, j + 1)) ++j;
-  s.add(j, __double2ll_rn(__dmul_rn(d, kFix)));
+  int j = clamp_bin(bin_guess(p, x), nb);
+  while (j > 0 && nn_lt(x, slab_edge(p, j))) --j;
+  while (j + 1 < nb && !nn_lt(x, slab_edge(p, j + 1))) ++j;
+  s.add(j, mcx::fix32_nonneg(d));
 }
 
 // Exact llrint((double)v * 2^32) for a finite float v >= 0, in integer

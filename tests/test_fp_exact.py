@@ -63,3 +63,32 @@ def test_two_u_minus_1_equals_the_fp64_expression(mc):
     for n in ns:
         u = n * 2.0**-53
         assert bits(mc.mc_two_u_minus_1(n)) == bits(2.0 * u - 1.0), n
+
+
+def test_llrint_nonneg_rounds_half_to_even(mc):
+    rng = random.Random(62)
+    vs = [rng.random() * 2.0 ** rng.randrange(-3, 62) for _ in range(100000)]
+    vs += [k + 0.5 for k in range(0, 50)] + [0.0, 0.49999999999999994, 0.5, 1.5, 2.5, 2.0**52 + 1, 2.0**61]
+    vs += [(2 * k + 1) * 2.0**-e for e in range(1, 40) for k in range(5)]
+    for v in vs:
+        assert mc.lib().mc_llrint_nonneg(v) == round(v), v  # Python's round: half to even
+
+
+def test_order_keys_compare_like_doubles(mc):
+    rng = random.Random(64)
+    special = [0.0, -0.0, 5e-324, -5e-324, 1.0, -1.0, 2.0**-1022, -(2.0**-1022), 1.7e308, -1.7e308]
+    xs = special + [rng.uniform(-1, 1) * 2.0 ** rng.randrange(-60, 60) for _ in range(3000)]
+    for i in range(0, len(xs) - 1):
+        for a, b in ((xs[i], xs[i + 1]), (xs[i + 1], xs[i]), (xs[i], xs[i])):
+            assert mc.lib().mc_d_lt(a, b) == int(a < b), (a, b)
+    for a in special:
+        for b in special:
+            assert mc.lib().mc_d_lt(a, b) == int(a < b), (a, b)
+
+
+def test_small_integer_products_round_once(mc):
+    rng = random.Random(11)
+    hs = [rng.uniform(0.001, 1000.0) for _ in range(3000)] + [100.0 / 64, 0.1, 1.0 / 3, 2.0**-20, 1.5625]
+    for h in hs:
+        for j in [0, 1, 2, 3, 7, 63, 64, 65, 1023, 2047] + [rng.randrange(2048) for _ in range(10)]:
+            assert bits(mc.mc_mul_small(j, h)) == bits(float(j) * h), (j, h)
