@@ -92,3 +92,4 @@ def test_small_integer_products_round_once(mc):
     for h in hs:
         for j in [0, 1, 2, 3, 7, 63, 64, 65, 1023, 2047] + [rng.randrange(2048) for _ in range(10)]:
             assert bits(mc.mc_mul_small(j, h)) == bits(float(j) * h), (j, h)
+
