@@ -143,6 +143,7 @@ enum { MC_SCHED_HISTORY = 0, MC_SCHED_EVENT = 1, MC_SCHED_AUTO = 2 };
 
 /* Box problem data (geometry MC_GEOM_BOX); host memory, read during the call. */
 #define MC_BOX_MAX_GROUPS 8
+#define MC_BOX_MAX_MESH 1024
 typedef struct {
     double side;                      /* cube [0,side]^3                           */
     double inner_lo, inner_hi;        /* inner region [inner_lo,inner_hi]^3        */
@@ -151,7 +152,7 @@ typedef struct {
     double ww_low[2], ww_high[2], ww_survive[2]; /* weight window per region       */
     double scatter_cdf[2][MC_BOX_MAX_GROUPS][MC_BOX_MAX_GROUPS]; /* [r][g][g'] CDF */
     uint32_t n_groups;
-    uint32_t mesh;                    /* mesh cells per axis (tally [mesh]^3)      */
+    uint32_t mesh;                    /* cells per axis (<= MC_BOX_MAX_MESH)        */
     uint32_t max_split;               /* cap on n of one split                     */
     uint32_t reserved;
 } mc_box_spec;

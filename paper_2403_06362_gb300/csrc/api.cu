@@ -141,7 +141,7 @@ int check_box(const mc_problem& q, uint32_t i) {
   }
   bool ok = b->side > 0.0 && std::isfinite(b->side) && b->inner_lo >= 0.0 && b->inner_lo < b->inner_hi &&
             b->inner_hi <= b->side && b->n_groups >= 1 && b->n_groups <= MC_BOX_MAX_GROUPS && b->mesh >= 1 &&
-            b->mesh <= 1024 && b->max_split >= 1 && b->reserved == 0 &&
+            b->mesh <= MC_BOX_MAX_MESH && b->max_split >= 1 && b->reserved == 0 &&
             (uint64_t)q.n_bins == (uint64_t)b->mesh * b->mesh * b->mesh;
   for (int r = 0; r < 2 && ok; ++r) {
     ok = b->sigma_t[r] > 0.0 && std::isfinite(b->sigma_t[r]) && b->c[r] >= 0.0 && b->c[r] <= 1.0 &&

@@ -117,6 +117,8 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
   __shared__ mcd::Affine tab[64];
   // A single problem's record is read on every flight: keep it in shared memory.
   __shared__ __align__(16) unsigned char s_prob[sizeof(BoxDev)];
+  // fp64, one problem: its mesh planes, read on every voxel crossing
+  __shared__ double s_planes[sizeof(T) == 8 ? mcb::kMaxPlanes : 1];
   if (threadIdx.x == 0) {
     mcd::Affine sq{a.lcg.g, a.lcg.c};
     for (int j = 0; j < 64; ++j) { tab[j] = sq; sq = mcd::compose(sq, sq); }
@@ -128,6 +130,12 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
   }
   __syncthreads();
   const BoxDev* probs = a.nprob == 1 ? reinterpret_cast<const BoxDev*>(s_prob) : a.probs;
+  const double* planes = nullptr;
+  if (sizeof(T) == 8 && a.nprob == 1) {
+    for (uint32_t j = threadIdx.x; j <= probs->mesh; j += blockDim.x) s_planes[j] = mcb::plane_of(*probs, (int)j);
+    __syncthreads();
+    planes = s_planes;
+  }
   const unsigned kFull = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
     } else {
       ++events;
       ++lc.flights;
-      const int o = mcb::box_flight<M, T>(*P, r, l, q, base);
+      const int o = mcb::box_flight<M, T>(*P, r, l, q, base, planes);
       if (o == mcb::kBoxLeak) {
         ++lc.leaks;
         end = true;

@@ -175,11 +175,18 @@ __device__ __forceinline__ T surface(const BoxDev& b, const Part<T>& q, int& kin
 __device__ __forceinline__ long long fix_of(double wl) { return mcx::fix32_nonneg(wl); }
 __device__ __forceinline__ long long fix_of(float wl) { return mcs::fix32_from_float(wl); }
 
-template <typename T> __device__ __forceinline__ T plane(const BoxDev& b, int j);
-template <> __device__ __forceinline__ double plane<double>(const BoxDev& b, int j) {
-  return j >= (int)b.mesh ? b.side : mcx::mul_small((uint32_t)j, b.h);  // RN(j h), mesh <= 1024
+// Mesh plane j: RN(j h) for j < mesh, side for j = mesh.  fp64: from the
+// caller's table (shared memory, one problem per launch) or computed as one
+// rounding of an exact integer product (mesh <= 1024).
+constexpr int kMaxPlanes = MC_BOX_MAX_MESH + 1;
+__device__ __forceinline__ double plane_of(const BoxDev& b, int j) {
+  return j >= (int)b.mesh ? b.side : mcx::mul_small((uint32_t)j, b.h);
 }
-template <> __device__ __forceinline__ float plane<float>(const BoxDev& b, int j) {
+template <typename T> __device__ __forceinline__ T plane(const BoxDev& b, const double* tab, int j);
+template <> __device__ __forceinline__ double plane<double>(const BoxDev& b, const double* tab, int j) {
+  return tab ? tab[j] : plane_of(b, j);
+}
+template <> __device__ __forceinline__ float plane<float>(const BoxDev& b, const double*, int j) {
   return j >= (int)b.mesh ? b.side_f : (float)j * b.h_f;
 }
 
@@ -196,7 +203,7 @@ template <> __device__ __forceinline__ int voxel_guess<float>(const BoxDev& b, f
 // t = (plane - p) / u, so every piece has the length the clipping definition
 // gives it.  base: this history's [mesh^3] slot row.
 template <typename T>
-__device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long* base) {
+__device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long* base, const double* tab) {
   const int nm = (int)b.mesh;
   const T h = sel<T>(b.h, b.h_f), inv_h = sel<T>(b.inv_h, b.inv_h_f);
   int idx[3];
@@ -204,12 +211,12 @@ __device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long
   for (int a = 0; a < 3; ++a) {
     int i = voxel_guess<T>(b, q.p[a]);
     i = i < 0 ? 0 : (i >= nm ? nm - 1 : i);
-    while (i > 0 && lt(q.p[a], plane<T>(b, i))) --i;
-    while (i + 1 < nm && !lt(q.p[a], plane<T>(b, i + 1))) ++i;
-    if (lt0(q.u[a]) && i > 0 && eq(q.p[a], plane<T>(b, i))) --i;
+    while (i > 0 && lt(q.p[a], plane<T>(b, tab, i))) --i;
+    while (i + 1 < nm && !lt(q.p[a], plane<T>(b, tab, i + 1))) ++i;
+    if (lt0(q.u[a]) && i > 0 && eq(q.p[a], plane<T>(b, tab, i))) --i;
     idx[a] = i;
-    if (gt0(q.u[a])) tn[a] = (plane<T>(b, i + 1) - q.p[a]) * q.inv[a];
-    else if (lt0(q.u[a])) tn[a] = (plane<T>(b, i) - q.p[a]) * q.inv[a];
+    if (gt0(q.u[a])) tn[a] = (plane<T>(b, tab, i + 1) - q.p[a]) * q.inv[a];
+    else if (lt0(q.u[a])) tn[a] = (plane<T>(b, tab, i) - q.p[a]) * q.inv[a];
     else tn[a] = T(INFINITY);
   }
   (void)h;
@@ -235,11 +242,11 @@ __device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long
     if (gt0(q.u[a])) {
       idx[a] += 1;
       if (idx[a] >= nm) break;
-      tn[a] = (plane<T>(b, idx[a] + 1) - q.p[a]) * q.inv[a];
+      tn[a] = (plane<T>(b, tab, idx[a] + 1) - q.p[a]) * q.inv[a];
     } else {
       idx[a] -= 1;
       if (idx[a] < 0) break;
-      tn[a] = (plane<T>(b, idx[a]) - q.p[a]) * q.inv[a];
+      tn[a] = (plane<T>(b, tab, idx[a]) - q.p[a]) * q.inv[a];
     }
   }
 }
@@ -259,7 +266,7 @@ __device__ __forceinline__ void box_source(const BoxDev& b, mcs::Rng<M>& r, cons
 // region (moved to the surface), or leak out of the box.
 template <int M, typename T>
 __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q,
-                                          unsigned long long* base) {
+                                          unsigned long long* base, const double* tab = nullptr) {
   int kind = 0;
   T ds = surface<T>(b, q, kind);
   bool collide;
@@ -287,7 +294,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
     }
   }
   const T len = collide ? d : ds;
-  trace<T>(b, q, len, base);
+  trace<T>(b, q, len, base, tab);
   for (int a = 0; a < 3; ++a) q.p[a] = q.p[a] + len * q.u[a];
   if (collide) return kBoxCollide;
   if (kind == 2) return kBoxLeak;
