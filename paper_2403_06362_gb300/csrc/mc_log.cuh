@@ -12,7 +12,8 @@
 //   ln x = e ln 2 + ln F + ln(1 + r),  r = (m - F) / F,  |r| < 2^-8,
 // where m - F is an exact integer difference, r is formed with a 64-bit
 // reciprocal of F (scale 2^71), ln(1 + r) comes from its series through r^8
-// by Horner's rule on 64-bit signed fixed point (scale 2^62), and the sum is
+// by Horner's rule on 64-bit signed fixed point (scale 2^62; the terms from
+// r^5 on, below 2^-42, on 32 bits), and the sum is
 // accumulated on 128 bits with scale 2^90 (ln 2 and ln F from 128-bit
 // tables).  For u < 2^-8 (x so close to 1 that e ln 2 + ln F would cancel)
 // -ln(1 - u) = u (1 + u/2 + ... + u^8/9) is used instead, relative to u.
@@ -102,6 +103,21 @@ __host__ __device__ __forceinline__ W128 add128(W128 a, W128 b) {
   return r;
 }
 
+__host__ __device__ __forceinline__ W128 sub128(W128 a, W128 b) {
+  W128 r;
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull);
+  return r;
+}
+
+__host__ __device__ __forceinline__ int mulhi32_(int a, int b) {
+#ifdef __CUDA_ARCH__
+  return __mulhi(a, b);
+#else
+  return (int)(((long long)a * b) >> 32);
+#endif
+}
+
 __host__ __device__ __forceinline__ W128 neg128(W128 a) {
   W128 r;
   r.lo = 0ull - a.lo;
@@ -139,6 +155,19 @@ __host__ __device__ __forceinline__ double w128_to_double(W128 a, int scale) {
   return from_bits(((biased - 1ull) << 52) + m53);  // the leading 1 adds one to the exponent
 }
 
+// The same for 2^82 <= a < 2^96 (the leading 1 at bit 82..95 of the high
+// word's range), without branches.
+__host__ __device__ __forceinline__ double w128_to_double_hi(W128 a, int scale) {
+  const int top = 127 - clz64_(a.hi);  // 82..95
+  const int sh = top - 63;             // 19..32
+  const uint64_t m64 = (a.hi << (64 - sh)) | (a.lo >> sh);
+  const bool sticky = (a.lo << (64 - sh)) != 0ull;
+  uint64_t m53 = m64 >> 11;
+  const uint64_t rest = m64 & 0x7FFull;
+  if (rest > 0x400ull || (rest == 0x400ull && (sticky || (m53 & 1ull)))) ++m53;
+  return from_bits(((uint64_t)(top - scale + 1022) << 52) + m53);
+}
+
 // ln(1 - u) for u = n 2^-53, 0 <= n < 2^53: a double <= 0 (+0 for n = 0).
 __host__ __device__ __forceinline__ double log1m_n(uint64_t n) {
 #ifdef __CUDA_ARCH__
@@ -169,29 +198,34 @@ __host__ __device__ __forceinline__ double log1m_n(uint64_t n) {
   const uint64_t ad = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
   const uint64_t pr = (umulhi_(ad, inv) << 19) | ((ad * inv) >> 45);  // |r| 2^71
   const long long R = D < 0 ? -(long long)pr : (long long)pr;
-  long long t = kLn1pC[7];
+  // ln(1 + r) = r (1 + r (c2 + r (c3 + r (c4 + r Q)))), Q = c5 + r (c6 + r (c7 + r c8)):
+  // |r^5 Q| < 2^-42, so Q needs only 32-bit arithmetic (scale 2^30, r at 2^39)
+  const int R32 = (int)(R >> 32);
+  int q = (int)(kLn1pC[7] >> 32);
+  q = (int)(kLn1pC[6] >> 32) + (mulhi32_(R32, q) >> 7);
+  q = (int)(kLn1pC[5] >> 32) + (mulhi32_(R32, q) >> 7);
+  q = (int)(kLn1pC[4] >> 32) + (mulhi32_(R32, q) >> 7);
+  long long t = (long long)q << 32;  // scale 2^62
 #pragma unroll
-  for (int k = 6; k >= 0; --k) t = kLn1pC[k] + (smulhi_(R, t) >> 7);  // scale 2^62
-  // ln(1 + r) 2^71 = (R t) >> 62, then to scale 2^90
+  for (int k = 3; k >= 0; --k) t = kLn1pC[k] + (smulhi_(R, t) >> 7);
+  // ln(1 + r) 2^71 = (R t) >> 62, then to scale 2^90 (sign-extended)
   const long long ph = smulhi_(R, t);
   const uint64_t pl = (uint64_t)R * (uint64_t)t;
   const long long p71 = (long long)(((uint64_t)ph << 2) | (pl >> 62));
-  W128 s;
-  s.lo = (uint64_t)p71 << 19;
-  s.hi = (uint64_t)(p71 >> 45);
-  // + ln F
+  W128 p;
+  p.lo = (uint64_t)p71 << 19;
+  p.hi = (uint64_t)(p71 >> 45);
+  // -ln x = |e| ln 2 - ln F - ln(1 + r) > 2^-8, on 128 bits with scale 2^90
+  const uint64_t ae = (uint64_t)(-e);
+  W128 a;
+  a.lo = ae * kLn2Lo;
+  a.hi = umulhi_(ae, kLn2Lo) + ae * kLn2Hi;
   W128 f;
   f.lo = MC_LOG_LD(kLnFLo, j);
   f.hi = MC_LOG_LD(kLnFHi, j);
-  s = add128(s, f);
-  // + e ln 2 (e < 0)
-  const uint64_t ae = (uint64_t)(-e);
-  W128 l2;
-  l2.lo = ae * kLn2Lo;
-  l2.hi = umulhi_(ae, kLn2Lo) + ae * kLn2Hi;
-  s = add128(s, neg128(l2));
+  a = sub128(sub128(a, f), p);
 #undef MC_LOG_LD
-  return -w128_to_double(neg128(s), 90);  // s < 0
+  return -w128_to_double_hi(a, 90);
 }
 
 // ln(1 - u) for a double u = n 2^-53 in [0, 1) (every uniform of the library).
