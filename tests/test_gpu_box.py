@@ -131,3 +131,20 @@ def test_box_full_size_sampled(env, oracle):
     c = counts_of(t)
     assert int(c[0]) == b["n_histories"] and int(c[12]) == 0
     assert int(c[0]) + int(c[14]) == int(c[6]) + int(c[11])
+
+
+def test_box_event_cap_matches_the_oracle_and_is_reported(env, oracle):
+    """A per-particle flight cap of 3: the capped particles, draws and tallies
+    equal the oracle's under the same cap, and mc_tally_read reports
+    MC_ERR_EVENT_CAP."""
+    mc, ctx, _ = env
+    b = W.box_problem(n_histories=3000, seeding=W.SEED_HASH)
+    t = gpu_box(env, b, event_cap=3)
+    L = oracle.Lcg(m=63, pad=0, g=W.LCG_G, c=1)
+    o = oracle.box_run(L, W.to_oracle_box(b, oracle), event_cap=3, per_history=True)
+    gc, oc = counts_of(t), o["counts"]
+    assert gc[12] > 0 and np.array_equal(gc[:15], oc[:15])
+    assert np.array_equal(t.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(t.bins.cpu().numpy().view(np.int64), o["tally"])
+    r = mc.mc_tally_read(ctx, t._keep[1], 0, t.c, check=False)
+    assert r.status == mc._ffi.MC_ERR_EVENT_CAP

@@ -143,3 +143,12 @@ def test_census_autotune_uses_whole_groups(env, oracle):
     o = oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle))
     assert np.array_equal(bins_of(t), o["tally"])
     del spec
+
+
+def test_census_event_cap_matches_the_oracle(env, oracle):
+    a = W.azurv1(n_reps=1, n_batches=4, per_batch=200, n_census=4)
+    t = run_gpu(env, a, event_cap=2)
+    o = oracle.azurv1_census_run(lcg(oracle), W.to_oracle_azurv1(a, oracle), event_cap=2)
+    gc, oc = names(oracle, counts_of(t)), names(oracle, o["counts"])
+    assert gc["capped"] > 0 and gc == oc
+    assert np.array_equal(bins_of(t), o["tally"])

@@ -126,3 +126,17 @@ def test_pulse_rejects_bad_stack_depth(env):
     a = W.azurv1(n_reps=1, n_batches=2, per_batch=10)
     with pytest.raises(mc.McError):
         run_gpu(env, a, stack_depth=257)
+
+
+@pytest.mark.parametrize("seeding", [W.SEED_HASH_HIER, W.SEED_STRIDE])
+def test_pulse_event_cap_matches_the_oracle_and_is_reported(env, oracle, seeding):
+    mc, ctx, _ = env
+    a = W.azurv1(seeding=seeding, n_reps=1, n_batches=5, per_batch=200)
+    t = run_gpu(env, a, event_cap=4)
+    o = oracle.azurv1_run(lcg(oracle), W.to_oracle_azurv1(a, oracle), event_cap=4, per_history=True)
+    gc, oc = counts_of(t), o["counts"]
+    assert gc[12] > 0 and np.array_equal(gc[:15], oc[:15])
+    assert np.array_equal(t.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(t.bins.cpu().numpy().view(np.int64), o["tally"])
+    r = mc.mc_tally_read(ctx, t._keep[1], 0, t.c, check=False)
+    assert r.status == mc._ffi.MC_ERR_EVENT_CAP
