@@ -501,6 +501,7 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     P.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 128;
     P.num_sms = ctx->num_sms;
     P.stack_depth = cfg->stack_depth ? cfg->stack_depth : 256u;
+    P.seeding = problems[0].seeding;
     if (problems[0].seeding != MC_SEED_STRIDE) {
       // overflow bank of 2^20 secondaries (32 MiB per generation bank)
       P.ovf_cap = 1ull << 20;

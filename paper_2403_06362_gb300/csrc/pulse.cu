@@ -91,7 +91,7 @@ struct PulseCounts {
   }
 };
 
-template <int M>
+template <int M, bool HASH>
 __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
   __shared__ mcd::Affine tab[64];
   __shared__ PulseDev sP;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
   __syncthreads();
   const PulseDev& P = sP;
   const mcd::Lcg l = a.lcg;
-  const bool hash_mode = P.seeding != MC_SEED_STRIDE;
+  constexpr bool hash_mode = HASH;  // (P.seeding != MC_SEED_STRIDE, chosen by the host)
   const unsigned kFull = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
     if (__ballot_sync(kFull, alive) == 0u) break;
     if (!alive) continue;
 
-    bool ended = false;
+    bool ended = false, redraw = false;
     if (events == a.event_cap) {
       ++lc.capped;
       ended = true;
@@ -213,43 +213,53 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
               ++lc.dropped;  // reported as MC_ERR_CAPACITY by mc_tally_read
             }
           }
-          mu = mcx::two_u_minus_1(r.next_n(l));
+          // its new direction: drawn in place (hash) or below, on the code path the
+          // pop shares (stride; measured faster for each variant)
+          if constexpr (HASH) mu = mcx::two_u_minus_1(r.next_n(l));
+          else redraw = true;
         } else {
           ++lc.absn;
           ended = true;
         }
       }
     }
-    if (!ended) continue;
-    // the current particle ended
-    if (hash_mode) {
-      fam_draws += r.draws;
-      if (r.draws > lc.maxd) lc.maxd = r.draws;
-      if (primary) {
-        if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
-        if (a.hist_draws) a.hist_draws[gi] = r.draws;
-        if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
+    if (ended) {  // the current particle ended
+      if (hash_mode) {
+        fam_draws += r.draws;
+        if (r.draws > lc.maxd) lc.maxd = r.draws;
+        if (primary) {
+          if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
+          if (a.hist_draws) a.hist_draws[gi] = r.draws;
+          if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
+        }
+      }
+      primary = false;
+      events = 0;
+      if (sp > 0) {  // the next secondary of the family; its direction below
+        --sp;
+        x = stack[sp].x;
+        t = stack[sp].t;
+        if constexpr (HASH) {
+          r = mcs::Rng<M>{stack[sp].seed, 0ull};
+          mu = mcx::two_u_minus_1(r.next_n(l));
+        } else {
+          redraw = true;
+        }
+      } else {
+        if (!hash_mode) {
+          fam_draws = r.draws;
+          if (r.draws > lc.maxd) lc.maxd = r.draws;
+          if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
+          if (a.hist_draws) a.hist_draws[gi] = r.draws;
+          if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
+        }
+        lc.draws += fam_draws;
+        alive = false;
       }
     }
-    primary = false;
-    events = 0;
-    if (sp > 0) {
-      --sp;
-      x = stack[sp].x;
-      t = stack[sp].t;
-      if (hash_mode) r = mcs::Rng<M>{stack[sp].seed, 0ull};
-      mu = mcx::two_u_minus_1(r.next_n(l));
-      continue;
-    }
-    if (!hash_mode) {
-      fam_draws = r.draws;
-      if (r.draws > lc.maxd) lc.maxd = r.draws;
-      if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
-      if (a.hist_draws) a.hist_draws[gi] = r.draws;
-      if (P.stride_q != 0 && r.draws > P.stride_q) { ++lc.exh; lc.exd += r.draws - P.stride_q; }
-    }
-    lc.draws += fam_draws;
-    alive = false;
+    // stride: one code path draws the direction of a scattered or a popped
+    // particle (the same draw, in the same stream order, as drawing it in place)
+    if (redraw) mu = mcx::two_u_minus_1(r.next_n(l));
   }
   lc.flush(a.counts);
 }
@@ -304,7 +314,9 @@ int pulse_run(const PulseLaunch& L, cudaStream_t s) {
   a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
   a.event_cap = L.event_cap;
   a.stack_depth = L.stack_depth;
-  auto k = L.lcg.m == 63 ? pulse_kernel<63> : pulse_kernel<0>;
+  const bool hash = L.seeding != MC_SEED_STRIDE;
+  auto k = L.lcg.m == 63 ? (hash ? pulse_kernel<63, true> : pulse_kernel<63, false>)
+                         : (hash ? pulse_kernel<0, true> : pulse_kernel<0, false>);
   int per_sm = 0;
   int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
                        "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
     if (__ballot_sync(kFull, alive) == 0u) break;
     if (!alive) continue;
 
-    bool ended = false, banked = false;
+    bool ended = false, banked = false, redraw = false;
     if (events == a.event_cap) {
       ++lc.capped;
       ended = true;
@@ -293,34 +293,35 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
               }
             }
           }
-          mu = mcx::two_u_minus_1(r.next_n(l));
+          redraw = true;  // its new direction, drawn below
         } else {
           ++lc.absn;
           ended = true;
         }
       }
     }
-    if (!ended) continue;
-    if (!banked) lc.stream_end(r.draws);
-    events = 0;
-    if (sp > 0) {  // next secondary of this family
-      --sp;
-      x = stack[sp].x;
-      t = stack[sp].t;
-      r = mcs::Rng<M>{stack[sp].seed, 0ull};
-      mu = mcx::two_u_minus_1(r.next_n(l));
-      continue;
+    if (ended) {
+      if (!banked) lc.stream_end(r.draws);
+      events = 0;
+      if (sp > 0) {  // next secondary of this family; its direction below
+        --sp;
+        x = stack[sp].x;
+        t = stack[sp].t;
+        r = mcs::Rng<M>{stack[sp].seed, 0ull};
+        redraw = true;
+      } else if (copies_left > 0) {  // next copy of the banked particle: Eq. (5) seed
+        --copies_left;
+        r = mcs::Rng<M>{mcd::hash64(next_key, s0) & l.mask, 0ull};
+        ++next_key;
+        x = x0;
+        t = a.t0;
+        mu = mu0;
+      } else {
+        alive = false;
+      }
     }
-    if (copies_left > 0) {  // next copy of the banked particle: Eq. (5) seed
-      --copies_left;
-      r = mcs::Rng<M>{mcd::hash64(next_key, s0) & l.mask, 0ull};
-      ++next_key;
-      x = x0;
-      t = a.t0;
-      mu = mu0;
-      continue;
-    }
-    alive = false;
+    // one code path draws the direction of a scattered or a popped particle
+    if (redraw) mu = mcx::two_u_minus_1(r.next_n(l));
   }
   lc.flush(a.counts);
 }

@@ -76,6 +76,7 @@ struct PulseLaunch {
   mc_lcg lcg;
   uint64_t event_cap;
   int block, num_sms;
+  uint32_t seeding;              // MC_SEED_*: selects the kernel variant
   uint32_t stack_depth;          // 1..256
   // Overflow bank (hash modes; pulse_ovf_bytes(ovf_cap) bytes; nullptr: a
   // full stack drops, MC_ERR_CAPACITY) and a pinned count for the host loop.
