@@ -514,17 +514,26 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             e["bits_identical_to_history"] = bool(torch.equal(tally.bins, hist_bins))
             res[f"{name}_{sname}_fp64_event"] = e
 
-    # Section 5: normality of the batch means, per bin, hash vs stride
+    # Section 5: normality of the batch means, per bin, hash vs stride; and
+    # the per-bin difference of the two tallies in standard errors (both
+    # estimate the same flux with independent streams, so z ~ N(0, 1))
     norm = {}
     for name, fn in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
+        reads = {}
         for sname, sd in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
             p = fn(sd)
             _, tally, cp = timed(p, reps=0, precision=0)
             r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream)
+            reads[sname] = r
             _, wv, pv = mc.mc_normality(r.batch)
             norm[f"{name}_{sname}"] = {"batches": int(r.batch.shape[0]), "points": int(r.batch.shape[1]),
                                        "fails_p_lt_0.05": int(np.sum(pv < 0.05)),
                                        "min_p": float(np.min(pv)), "median_p": float(np.median(pv))}
+        h, st = reads["hash"], reads["stride"]
+        se = np.sqrt((h.rel_err * h.flux) ** 2 + (st.rel_err * st.flux) ** 2)
+        z = (h.flux - st.flux) / np.where(se > 0, se, 1.0)
+        norm[f"{name}_hash_minus_stride"] = {"bins": int(z.size), "max_abs_z": float(np.max(np.abs(z))),
+                                             "mean_z": float(np.mean(z)), "bins_abs_z_gt_3": int(np.sum(np.abs(z) > 3))}
     res["normality"] = norm
 
     # 256 batched slab problems
