@@ -18,6 +18,13 @@
 // the history schedule.  The host launches iterations in batches (optionally
 // as one captured CUDA graph per batch) and reads the completion flag between
 // batches; no kernel waits on another.
+//
+// Once every history has started and the live particles no longer fill the
+// GPU (at most tail_threshold), an iteration moves too few particles to pay
+// for its five launches, and the longest chain would set the iteration
+// count.  The advance kernel then flags the switch, and one tail kernel runs
+// each live particle to its end from the bank, with the same slab_flight and
+// slab_collide: the same draws and the same integer contributions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,6 +61,7 @@ struct EvBank {
 };
 
 struct EvArgs {
+  uint32_t tail_threshold;  // live particles at or below which the tail kernel takes over
   const SlabDev* probs;
   uint32_t nprob;
   uint64_t range_begin, total;
@@ -305,8 +313,46 @@ __global__ void ev_advance_kernel(EvArgs a) {
   c->ncq = 0;
   c->cur = cur ^ 1u;
   const unsigned int live = c->nfq[cur ^ 1u];
-  c->done = (live == 0 && c->ticket >= a.total) ? 1u : 0u;
+  // 1: finished; 2: every history started and few enough live for the tail kernel
+  c->done = c->ticket < a.total ? 0u : (live == 0 ? 1u : (live <= a.tail_threshold ? 2u : 0u));
   c->iters += 1;
+}
+
+// The tail: each live particle of the current flight queue flies and
+// collides to the end of its history in one thread.
+template <int M, bool F32>
+__global__ void __launch_bounds__(256) ev_tail_kernel(EvArgs a) {
+  const EvBank& b = a.b;
+  const unsigned int cur = b.ctl->cur;
+  const uint32_t n = b.ctl->nfq[cur];
+  const uint32_t* fq = cur ? b.fq1 : b.fq0;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = tid; t < n; t += nt) {
+    const uint32_t slot = fq[t];
+    const SlabDev& P = a.probs[b.prob[slot]];
+    mcs::Rng<M> r{b.rng[slot], b.draws[slot]};
+    uint64_t ev = b.events[slot];
+    uint32_t co = 0, sc = 0;
+    mcs::SlabParticle q{};
+    if constexpr (F32) {
+      q.xf = b.xf[slot]; q.muf = b.muf[slot]; q.wf = b.wf[slot];
+    } else {
+      q.x = b.x[slot]; q.mu = b.mu[slot]; q.w_mu = b.w[slot];
+    }
+    const mcs::Sink sink{a.tally + b.tbase[slot]};
+    int outcome;
+    for (;;) {
+      if (ev == a.event_cap) { outcome = -1; break; }
+      ++ev;
+      outcome = mcs::slab_event<M, F32>(P, r, a.lcg, q, sink, co, sc);
+      if (outcome != mcs::kContinue) break;
+    }
+    b.events[slot] = ev;
+    b.coll[slot] += co;
+    b.scat[slot] += sc;
+    ev_finish(a, slot, outcome, r.x, r.draws);
+  }
 }
 
 constexpr int kIterPerBatch = 32;
@@ -356,6 +402,11 @@ int run_event(const EvArgs& a, int grid, cudaStream_t capture_stream, unsigned i
     cudaError_t e = cudaMemcpyAsync(h_done, &a.b.ctl->done, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = mci::cuda_status(e, "event schedule completion check"); break; }
+    if (*h_done == 2u) {  // the rest of the histories in one kernel
+      ev_tail_kernel<M, F32><<<grid, 256, 0, s>>>(a);
+      st = mci::cuda_status(cudaGetLastError(), "ev_tail_kernel launch");
+      break;
+    }
     if (*h_done) break;
   }
   if (exec) cudaGraphExecDestroy(exec);
@@ -383,6 +434,7 @@ int slab_event_run(const SlabLaunch& L, void* d_bank, uint32_t cap, unsigned int
   a.event_cap = L.event_cap;
   carve(d_bank, cap, &a.b);
   const int grid = std::max(1, L.num_sms * 4);
+  a.tail_threshold = (uint32_t)L.num_sms * 1024u;
   // Every iteration flies each live particle once, so the longest history
   // bounds the iteration count; the cap below is a safety net only.
   const uint64_t max_iters = std::min<uint64_t>(L.event_cap, 1ull << 36) * 2 + (L.total / cap + 2) * 4 + 64;
