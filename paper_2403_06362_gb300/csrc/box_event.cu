@@ -37,6 +37,7 @@ struct Bank {
 };
 
 struct Args {
+  uint32_t tail_threshold;  // live particles at or below which the tail kernel takes over
   const BoxDev* probs;
   uint32_t nprob;
   const ChildRec* child_in;  // nullptr: source histories
@@ -306,8 +307,58 @@ __global__ void advance_kernel(Args a) {
   c->ncq = 0;
   c->cur = cur ^ 1u;
   const unsigned int live = c->nfq[cur ^ 1u];
-  c->done = (live == 0 && c->ticket >= a.total) ? 1u : 0u;
+  // 1: finished; 2: every particle of the generation started and few enough
+  // live for the tail kernel
+  c->done = c->ticket < a.total ? 0u : (live == 0 ? 1u : (live <= a.tail_threshold ? 2u : 0u));
   c->iters += 1;
+}
+
+// The tail of a generation: each live particle of the current flight queue
+// flies, crosses and collides to its end in one thread (split children go
+// to the child bank as in collide_kernel).
+template <int M, typename T>
+__global__ void __launch_bounds__(256) tail_kernel(Args a) {
+  const Bank& b = a.b;
+  const unsigned int cur = b.ctl->cur;
+  const uint32_t n = b.ctl->nfq[cur];
+  const uint32_t* fq = cur ? b.fq1 : b.fq0;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = tid; t < n; t += nt) {
+    const uint32_t s = fq[t];
+    const uint32_t pi = b.prob[s];
+    const BoxDev& P = a.probs[pi];
+    mcs::Rng<M> r{b.rng[s], b.draws[s]};
+    mcb::Part<T> q;
+    load_part<T>(b, s, q);
+    unsigned long long* const base = a.tally + b.tbase[s];
+    uint64_t ev = b.events[s];
+    uint32_t co = b.coll[s];
+    int outcome;
+    for (;;) {
+      if (ev == a.event_cap) { outcome = -1; break; }
+      ++ev;
+      const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, base);
+      if (o == mcb::kBoxLeak) { outcome = o; break; }
+      if (o != mcb::kBoxCollide) continue;  // crossed into the other region
+      ++co;
+      const int c = mcb::box_collide<M, T>(P, r, a.lcg, q);
+      if (c == mcb::kBoxKilled) { outcome = c; break; }
+      if (c >= mcb::kSplitBase + 2) {
+        const uint32_t ns = (uint32_t)(c - mcb::kSplitBase);
+        unsigned long long* cn = a.counts + (size_t)pi * MC_NCOUNT;
+        atomicAdd(cn + MC_C_SPLITS, 1ull);
+        atomicAdd(cn + MC_C_CHILDREN, (unsigned long long)(ns - 1));
+        for (uint32_t k = 0; k + 1 < ns; ++k) {
+          const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
+          if (idx < a.child_cap)
+            mcb::store_child<T>(a.child_out[idx], q, mcb::child_seed(k, r.x, a.lcg.mask), pi, b.tbase[s]);
+        }
+      }
+    }
+    b.events[s] = ev;
+    b.coll[s] = co;
+    finish(a, s, outcome, r.x, r.draws);
+  }
 }
 
 constexpr int kIter = 32;
@@ -363,6 +414,11 @@ int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_
       st = mci::cuda_status(e, "box event batch");
       break;
     }
+    if (*L.h_done == 2u) {  // the rest of the generation in one kernel
+      tail_kernel<M, T><<<grid, 256, 0, s>>>(a);
+      st = mci::cuda_status(cudaGetLastError(), "box tail_kernel launch");
+      break;
+    }
     if (*L.h_done) break;
   }
   if (exec) cudaGraphExecDestroy(exec);
@@ -383,6 +439,7 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
   a.event_cap = L.event_cap;
   carve(L.d_bank, L.bank_cap, &a.b);
   const int grid = std::max(1, L.num_sms * 4);
+  a.tail_threshold = (uint32_t)L.num_sms * 1024u;
   ChildRec* bank[2] = {static_cast<ChildRec*>(L.d_child[0]), static_cast<ChildRec*>(L.d_child[1])};
   unsigned long long* cnt[2] = {L.d_child_count, L.d_child_count + 1};
   for (uint64_t start = 0; start < L.total; start += L.primary_chunk) {
