@@ -126,6 +126,7 @@ def lib():
             L.or_box_trace.restype = None; L.or_box_trace.argtypes = [BP, P, P, dbl, dbl, P, P]
             L.or_box_surface_dist.restype = dbl
             L.or_box_surface_dist.argtypes = [BP, P, P, u32, C.POINTER(C.c_int)]
+            L.or_box_next_group.restype = u32; L.or_box_next_group.argtypes = [BP, u32, u32, dbl]
             AP = C.POINTER(Azurv1Problem)
             L.or_azurv1_seed.restype = u64; L.or_azurv1_seed.argtypes = [C.POINTER(Lcg), AP, u64]
             L.or_azurv1_run.restype = C.c_int
@@ -345,6 +346,11 @@ def box_surface_dist(prob: BoxProblem, p, u, region):
     k = C.c_int(0)
     d = float(lib().or_box_surface_dist(C.byref(prob), _ptr(p), _ptr(u), region, C.byref(k)))
     return d, int(k.value)
+
+
+def box_next_group(prob: BoxProblem, region: int, g: int, u: float) -> int:
+    """The downscatter group the box transport picks for uniform u."""
+    return int(lib().or_box_next_group(C.byref(prob), region, g, u))
 
 
 # --- the paper's supercritical time-dependent problem (mc_oracle_azurv1.c) -------

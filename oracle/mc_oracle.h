@@ -97,6 +97,7 @@ void or_box_trace(const or_box_problem* b, const double* p, const double* u, dou
                   double* tfp);
 double or_box_surface_dist(const or_box_problem* b, const double* p, const double* u, uint32_t region,
                            int* kind_out);
+uint32_t or_box_next_group(const or_box_problem* b, uint32_t region, uint32_t g, double u);
 
 /* The paper's supercritical time-dependent problem (mc_oracle_azurv1.c). */
 typedef struct {

@@ -177,6 +177,13 @@ static void push(stack_t_* s, const part_t* p) {
 }
 
 /* Follows one particle to its end; pushes the children of its splits. */
+/* Downscatter: the first group g' >= g with u < CDF[region][g][g'] (R18). */
+static uint32_t next_group(const or_box_problem* b, uint32_t rg, uint32_t g, double u) {
+    for (uint32_t k = g; k < b->n_groups; ++k)
+        if (u < b->cdf[rg][g][k]) return k;
+    return g;
+}
+
 static int follow(const or_lcg* l, const or_box_problem* b, part_t* q, uint64_t event_cap, int64_t* t64,
                   double* tfp, uint64_t* cnt, stack_t_* st) {
     rng_t r = {q->rng, q->draws, l->m, l->g, l->c};
@@ -224,15 +231,7 @@ static int follow(const or_lcg* l, const or_box_problem* b, part_t* q, uint64_t 
         cnt[OR_C_COLLISIONS]++;
         const uint32_t rg = q->region;
         q->w = q->w * b->c[rg];
-        double ug = next_u(&r);
-        uint32_t g2 = q->g;
-        for (uint32_t k = q->g; k < b->n_groups; ++k) {
-            if (ug < b->cdf[rg][q->g][k]) {
-                g2 = k;
-                break;
-            }
-        }
-        q->g = g2;
+        q->g = next_group(b, rg, q->g, next_u(&r));
         iso_dir(&r, q->u);
         set_inv(q->u, inv);
         cnt[OR_C_SCATTERS]++;
@@ -317,7 +316,12 @@ int or_box_run(const or_lcg* l, const or_box_problem* b, uint64_t id_begin, uint
     return status;
 }
 
-/* Test hooks: one isotropic direction from a state; the segment tally. */
+/* Test hooks: one isotropic direction from a state; the segment tally; the
+ * downscatter group choice. */
+uint32_t or_box_next_group(const or_box_problem* b, uint32_t region, uint32_t g, double u) {
+    return next_group(b, region, g, u);
+}
+
 uint64_t or_box_iso_dir(const or_lcg* l, uint64_t x, double* u_out) {
     rng_t r = {x, 0, l->m, l->g, l->c};
     iso_dir(&r, u_out);

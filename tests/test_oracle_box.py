@@ -152,3 +152,49 @@ def test_box_seeds(oracle):
     assert oracle.box_seed(L, b, 5) == oracle.hash_seed(5, 42, 63)
     bs = box(oracle, n_histories=10, seeding=W.SEED_STRIDE)
     assert oracle.box_seed(L, bs, 5) == oracle.stride_seed(1, W.STRIDE_Q, 5, 63, G, 1)
+
+
+def test_group_choice_follows_the_cdf_rows(oracle):
+    """Downscatter (R18): the group picked for u uniform on [0, 1) is g' with
+    probability CDF[g'] - CDF[g' - 1] (chi-square per row), and a u on a row
+    boundary belongs to the next group (u < CDF strictly)."""
+    from scipy.stats import chi2
+    P = W.to_oracle_box(W.box_problem(n_histories=1), oracle)
+    us = np.random.default_rng(11).random(40000)
+    for rg in range(2):
+        for g in range(int(P.n_groups)):
+            cdf = np.array([P.cdf[rg][g][k] for k in range(int(P.n_groups))])
+            prob = np.diff(np.concatenate([[0.0], cdf]))
+            picks = np.array([oracle.box_next_group(P, rg, g, float(u)) for u in us])
+            assert picks.min() >= g  # downscatter only
+            obs = np.bincount(picks, minlength=len(prob)).astype(float)
+            live = prob > 0
+            stat = np.sum((obs[live] - len(us) * prob[live]) ** 2 / (len(us) * prob[live]))
+            assert chi2.sf(stat, max(int(live.sum()) - 1, 1)) > 1e-4, (rg, g, obs, prob)
+            for k in range(g, int(P.n_groups) - 1):
+                if cdf[k] > 0:
+                    assert oracle.box_next_group(P, rg, g, float(cdf[k])) > k
+
+
+def test_mesh_tally_is_symmetric(oracle):
+    """The box, its inner cube, the uniform isotropic source and the weight
+    windows are symmetric under axis permutations and under x -> side - x,
+    so the expected mesh tally is too: the three axis profiles agree, and
+    each equals its mirror image, within batch errors."""
+    b = W.box_problem(n_histories=6000, seeding=W.SEED_HASH, n_batches=12)
+    L = oracle.Lcg(m=63, pad=0, g=W.LCG_G, c=1)
+    t = oracle.box_run(L, W.to_oracle_box(b, oracle))["tally"].astype(np.float64)
+    nm = b["mesh"]
+    t = t.reshape(12, nm, nm, nm)  # [batch][z][y][x]
+    prof = {"x": t.sum(axis=(1, 2)), "y": t.sum(axis=(1, 3)), "z": t.sum(axis=(2, 3))}  # [batch][i]
+
+    def close(a, c):
+        d = a - c  # per batch, per bin
+        se = d.std(axis=0, ddof=1) / np.sqrt(d.shape[0])
+        z = d.mean(axis=0) / np.where(se > 0, se, np.inf)
+        return np.abs(z).max()
+
+    assert close(prof["x"], prof["y"]) < 5.0
+    assert close(prof["x"], prof["z"]) < 5.0
+    for ax in "xyz":
+        assert close(prof[ax], prof[ax][:, ::-1]) < 5.0
