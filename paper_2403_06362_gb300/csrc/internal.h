@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "../../include/mc.h"
 
@@ -54,6 +55,13 @@ struct mc_ctx {
   void* h_problems = nullptr;
   size_t h_problems_bytes = 0;
   cudaEvent_t staged = nullptr;  // recorded after the last upload from h_problems
+  // Host image of the problem records last uploaded and prepared: a call with
+  // the same records (same kind and count) finds the device copy current and
+  // skips the upload and the prep kernel.
+  std::vector<unsigned char>* staged_image = nullptr;
+  std::vector<unsigned char>* fill_scratch = nullptr;
+  int staged_kind = -1;
+  uint32_t staged_n = 0;
   // Event-based schedule: particle bank and a pinned completion flag.
   mci::DeviceBuf bank;
   unsigned int* h_done = nullptr;

@@ -119,6 +119,12 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
     for (uint32_t s = threadIdx.x; s < a.smem_slots; s += blockDim.x) s_tally[s] = 0ull;
   }
   double* s_edges = a.smem_edges ? reinterpret_cast<double*>(s_tally + (SMEM ? a.smem_slots : 0u)) : nullptr;
+  double* s_widths = s_edges ? s_edges + a.smem_edges : nullptr;  // n_bins widths after the edges
+  if (s_edges) {
+    const SlabDev& p0 = a.probs[0];
+    for (uint32_t j = threadIdx.x; j + 1 < a.smem_edges; j += blockDim.x)
+      s_widths[j] = __dsub_rn(mcs::slab_edge(p0, (int)j + 1), mcs::slab_edge(p0, (int)j));
+  }
   if (s_edges) {
     const SlabDev& p0 = a.probs[0];
     for (uint32_t j = threadIdx.x; j < a.smem_edges; j += blockDim.x) s_edges[j] = mcs::slab_edge(p0, (int)j);
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
   const SlabDev* P = a.probs;
   mcs::Rng<M> r{0ull, 0ull};
   mcs::SlabParticle q{};
-  mcs::Sink sink{nullptr, s_edges};
+  mcs::Sink sink{nullptr, s_edges, s_widths};
   uint64_t gi = 0, events = 0;
 
   for (;;) {
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
 template <int M, bool F32, bool SMEM>
 int launch_history(const RunArgs& a, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
   auto k = slab_history_kernel<M, F32, SMEM>;
-  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 8u;
+  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u;  // edges + widths
   if (smem > 48u * 1024u) {
     int st = mci::cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               "cudaFuncSetAttribute(slab_history_kernel)");

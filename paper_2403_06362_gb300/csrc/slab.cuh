@@ -104,6 +104,7 @@ __device__ __forceinline__ int clamp_bin(int j, int nb) { return j < 0 ? 0 : (j 
 struct Sink {
   unsigned long long* base;  // this history's [bin] row (smem or global)
   const double* edges;
+  const double* widths;  // with edges: widths[j] = e_{j+1} - e_j (the same fp64 difference)
   __device__ __forceinline__ void add(int j, long long v) const {
     if (v != 0) atomicAdd(base + j, (unsigned long long)v);
   }
@@ -131,6 +132,24 @@ __device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, doub
   int j = clamp_bin(bin_guess(p, a), nb);
   while (j > 0 && nn_lt(a, edge_of(p, s, j))) --j;
   while (j + 1 < nb && !nn_lt(a, edge_of(p, s, j + 1))) ++j;
+  if (s.widths) {
+    // The same walk with the interior bins' lengths from the width table:
+    // the first bin [a, min(b, e_{j+1})], the whole bins while e_{j+1} <= b,
+    // the last [e_j, b]; only the ends take an fp64 difference.
+    double e1 = s.edges[j + 1];
+    const double hi = nn_lt(b, e1) ? b : e1;
+    if (nn_lt(a, hi)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(hi, a), w_fix)));
+    if (!nn_lt(e1, b) || j + 1 >= nb) return;
+    for (++j;; ++j) {
+      e1 = s.edges[j + 1];
+      if (nn_lt(b, e1)) break;
+      s.add(j, mcx::llrint_nonneg(__dmul_rn(s.widths[j], w_fix)));
+      if (!nn_lt(e1, b) || j + 1 >= nb) return;
+    }
+    const double ej = s.edges[j];
+    if (nn_lt(ej, b)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(b, ej), w_fix)));
+    return;
+  }
   double lo = a;
   for (;;) {
     const double e1 = edge_of(p, s, j + 1);
