@@ -422,6 +422,14 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   L.smem_slots = stage ? (uint32_t)tally->n_slots : 0u;
   L.f32 = cfg->precision == MC_FP32_GUARDED;
   L.block = cfg->block ? (int)cfg->block : 256;
+  if (!cfg->block) {
+    // A run too small to give every SM a block of 256 threads is spread over
+    // all SMs in smaller blocks: its time is the latency of its longest warps,
+    // which run faster with fewer warps per sub-partition.
+    const uint64_t warps = (L.total + L.chunk - 1) / L.chunk;
+    if (warps * 32 < (uint64_t)ctx->num_sms * 256)
+      L.block = (int)std::max<uint64_t>(32, 32 * std::max<uint64_t>(1, warps / (uint64_t)ctx->num_sms));
+  }
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
   *out = L;
