@@ -227,7 +227,7 @@ def main():
     ap.add_argument("--no-detail", action="store_true")
     ap.add_argument("--profile-workload", default=None,
                     choices=["slab_long_fp64", "slab_long_fp32", "slab_small_fp64", "box_fp32", "box_fp64",
-                             "batched_fp32", "pulse_hash", "pulse_stride", "pulse_census"],
+                             "batched_fp32", "batched_fp64", "pulse_hash", "pulse_stride", "pulse_census"],
                     help="run one transport workload (a warm-up run, then one run) and exit; for profilers")
     ap.add_argument("--histories", type=int, default=0, help="history count for --profile-workload")
     args = ap.parse_args()

@@ -81,6 +81,14 @@ namespace {
 constexpr size_t kTicketOff = 0;     // unsigned long long ticket
 constexpr size_t kScratchBytes = 256;
 
+// Slab records are followed, 256-byte aligned, by every problem's bin edge
+// and width tables (filled on the device by slab_prep).
+size_t slab_tables_offset(uint32_t n) { return ((size_t)n * mci::slab_dev_size() + 255u) & ~(size_t)255u; }
+size_t slab_stage_bytes(const mc_problem* problems, uint32_t n) {
+  return slab_tables_offset(n) + (size_t)mci::slab_table_doubles(problems, n) * sizeof(double);
+}
+void* slab_tables_of(mc_ctx* ctx, uint32_t n) { return static_cast<char*>(ctx->problems.ptr) + slab_tables_offset(n); }
+
 // Host half of staging: waits until the pinned buffer is free, sizes the
 // buffers and writes the problem records into pinned memory.
 int stage_host(mc_ctx* ctx, const mc_problem* problems, uint32_t n, size_t* bytes_out) {
@@ -98,7 +106,7 @@ int stage_host(mc_ctx* ctx, const mc_problem* problems, uint32_t n, size_t* byte
     MC_TRY_CUDA(cudaMallocHost(&ctx->h_problems, bytes));
     ctx->h_problems_bytes = bytes;
   }
-  int st = ctx->problems.reserve(bytes);
+  int st = ctx->problems.reserve(box ? bytes : slab_stage_bytes(problems, n));
   if (st != MC_OK) return st;
   if (box) mci::box_fill_host(problems, n, ctx->h_problems);
   else mci::slab_fill_host(problems, n, ctx->h_problems);
@@ -113,6 +121,7 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
   const bool pulse = problems[0].geometry == MC_GEOM_PULSE;
   const size_t bytes = pulse ? mci::pulse_dev_size()
                              : (size_t)n * (box ? mci::box_dev_size() : mci::slab_dev_size());
+  const size_t dev_bytes = (pulse || box) ? bytes : slab_stage_bytes(problems, n);
   // Fill a host image first: if it equals the image last uploaded, the
   // device copy (base fields and the derived ones the prep kernel computes
   // from them) is still current.
@@ -124,7 +133,7 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
   if (pulse) mci::pulse_fill_host(problems, img.data());
   else if (box) mci::box_fill_host(problems, n, img.data());
   else mci::slab_fill_host(problems, n, img.data());
-  if (kind == ctx->staged_kind && n == ctx->staged_n && ctx->problems.bytes >= bytes &&
+  if (kind == ctx->staged_kind && n == ctx->staged_n && ctx->problems.bytes >= dev_bytes &&
       *ctx->staged_image == img)
     return MC_OK;
   cudaEvent_t* ev = &ctx->staged;
@@ -137,14 +146,15 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
     ctx->h_problems_bytes = bytes;
   }
   ctx->staged_kind = -1;  // until the upload below is enqueued
-  int st = ctx->problems.reserve(bytes);
+  int st = ctx->problems.reserve(dev_bytes);
   if (st != MC_OK) return st;
   std::memcpy(ctx->h_problems, img.data(), bytes);
   MC_TRY_CUDA(cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, s));
   if (!*ev) MC_TRY_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
   MC_TRY_CUDA(cudaEventRecord(*ev, s));
   st = pulse ? mci::pulse_prep(ctx->problems.ptr, s)
-             : (box ? mci::box_prep(ctx->problems.ptr, n, s) : mci::slab_prep(ctx->problems.ptr, n, s));
+             : (box ? mci::box_prep(ctx->problems.ptr, n, s)
+                    : mci::slab_prep(ctx->problems.ptr, n, s, slab_tables_of(ctx, n)));
   if (st != MC_OK) return st;
   ctx->staged_image->swap(img);
   ctx->staged_kind = kind;
@@ -399,6 +409,7 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   mci::SlabLaunch L{};
   L.single_n_bins = n_problems == 1 ? problems[0].n_bins : 0u;
   L.d_probs = ctx->problems.ptr;
+  L.d_tables = slab_tables_of(ctx, n_problems);
   L.n_problems = n_problems;
   // Default chunk: about four grabs per resident warp (fine-grained enough to
   // balance long-tailed histories, coarse enough that lanes rarely change
@@ -474,7 +485,7 @@ int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, u
     cudaGraph_t g = nullptr;
     MC_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, cs);
-    mci::slab_prep(ctx->problems.ptr, n_problems, cs);
+    mci::slab_prep(ctx->problems.ptr, n_problems, cs, slab_tables_of(ctx, n_problems));
     if (!cfg->accumulate) {
       cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), cs);
       cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), cs);

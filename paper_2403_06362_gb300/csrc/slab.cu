@@ -27,6 +27,19 @@ namespace {
 
 using mcs::SlabDev;
 
+// Bin edge and width tables of every problem, after the records (`tables`
+// may be null: no tables).
+__global__ void slab_tables_kernel(const SlabDev* __restrict__ p, uint32_t n, double* __restrict__ tables) {
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const SlabDev& q = p[i];
+    double* e = tables + q.tab_off;
+    double* w = e + q.n_bins + 1;
+    for (uint32_t j = threadIdx.x; j <= q.n_bins; j += blockDim.x) e[j] = mcs::slab_edge(q, (int)j);
+    for (uint32_t j = threadIdx.x; j < q.n_bins; j += blockDim.x)
+      w[j] = __dsub_rn(mcs::slab_edge(q, (int)j + 1), mcs::slab_edge(q, (int)j));
+  }
+}
+
 __global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     SlabDev& q = p[i];
@@ -68,6 +81,7 @@ struct RunArgs {
   uint64_t event_cap;
   uint32_t smem_slots;
   uint32_t smem_edges;  // single-problem launches: n_bins + 1 edges in shared memory (0: none)
+  const double* tables; // else per-problem edge and width tables in global memory (nullable)
 };
 
 // Per-lane counters for the lane's current problem.
@@ -170,6 +184,10 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
         const uint64_t id = gi - P->hist_begin;
         const uint64_t batch = mcs::batch_of(id, P->n_hist, P->n_batches);
         sink.base = (SMEM ? s_tally : a.tally) + P->tally_offset + batch * P->n_bins;
+        if (a.tables) {
+          sink.edges = a.tables + P->tab_off;
+          sink.widths = sink.edges + P->n_bins + 1;
+        }
         r.x = mcs::slab_seed(*P, id, tab, l.mask);
         r.draws = 0;
         mcs::slab_source<M, F32>(*P, r, l, q);
@@ -258,6 +276,7 @@ size_t slab_dev_size() { return sizeof(SlabDev); }
 
 void slab_fill_host(const mc_problem* src, uint32_t n, void* dst) {
   SlabDev* d = static_cast<SlabDev*>(dst);
+  uint64_t off = 0;
   for (uint32_t i = 0; i < n; ++i) {
     SlabDev q;
     std::memset(&q, 0, sizeof q);
@@ -274,13 +293,25 @@ void slab_fill_host(const mc_problem* src, uint32_t n, void* dst) {
     q.n_batches = src[i].n_batches;
     q.source = src[i].source;
     q.seeding = src[i].seeding;
+    q.tab_off = off;
+    off += 2ull * q.n_bins + 1ull;
     d[i] = q;
   }
 }
 
-int slab_prep(void* d_probs, uint32_t n, cudaStream_t s) {
+int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables) {
   slab_prep_kernel<<<1, 256, 0, s>>>(static_cast<SlabDev*>(d_probs), n);
-  return cuda_status(cudaGetLastError(), "slab_prep_kernel launch");
+  int st = cuda_status(cudaGetLastError(), "slab_prep_kernel launch");
+  if (st != MC_OK || !d_tables) return st;
+  slab_tables_kernel<<<std::min<uint32_t>(n, 1024u), 64, 0, s>>>(static_cast<const SlabDev*>(d_probs), n,
+                                                                   static_cast<double*>(d_tables));
+  return cuda_status(cudaGetLastError(), "slab_tables_kernel launch");
+}
+
+uint64_t slab_table_doubles(const mc_problem* src, uint32_t n) {
+  uint64_t t = 0;
+  for (uint32_t i = 0; i < n; ++i) t += 2ull * src[i].n_bins + 1ull;
+  return t;
 }
 
 int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
@@ -304,6 +335,8 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
     // bin count comes from the host copy through the launch descriptor)
     if (L.single_n_bins + 1 <= 4096) a.smem_edges = L.single_n_bins + 1;
   }
+  // otherwise each problem's tables in global memory, where staged
+  a.tables = a.smem_edges ? nullptr : static_cast<const double*>(L.d_tables);
   if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
   return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
 }

@@ -38,6 +38,8 @@ struct SlabDev {
   float L_f, h_f, inv_h_f, inv_st_f;
   uint64_t seed_hash;   // hash seeding: seed half of hash(., s) or of hash(., hash(key, s))
   uint64_t hist_begin;  // global index of local history 0
+  uint64_t tab_off;     // its edge table (n_bins + 1) and width table (n_bins) in the table
+                        // area after the records, in doubles (set on the host)
 };
 
 constexpr double kFix = 4294967296.0;  // 2^32: fixed-point scale of the tallies

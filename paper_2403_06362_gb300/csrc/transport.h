@@ -21,13 +21,17 @@ struct SlabLaunch {
   uint64_t event_cap;
   uint32_t smem_slots;         // 0 = global atomics; else slots staged in smem
   uint32_t single_n_bins;      // n_bins of the problem when n_problems == 1
+  const void* d_tables = nullptr;  // per-problem edge and width tables (nullable; see slab_prep)
   bool f32;
   int block, blocks_per_sm, num_sms;
 };
 
 size_t slab_dev_size();
 void slab_fill_host(const mc_problem* src, uint32_t n, void* dst);
-int slab_prep(void* d_probs, uint32_t n, cudaStream_t s);
+// d_tables (nullable): room for slab_table_doubles(...) doubles, filled
+// with every problem's bin edges and widths.
+int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables = nullptr);
+uint64_t slab_table_doubles(const mc_problem* src, uint32_t n);
 int slab_history_launch(const SlabLaunch& L, cudaStream_t s);
 
 // Event-based schedule (slab_event.cu): bank of `cap` particles in d_bank

@@ -113,6 +113,37 @@ def test_ranges_accumulate_to_the_same_bits(env):
     assert np.array_equal(c1[:, :13], c0[:, :13])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bin_tables_in_global_memory(env, oracle, precision):
+    """Bin edge and width tables read from global memory: one problem with
+    more bins than the shared-memory table holds, and a batched launch with
+    uneven bin counts; fp64 tallies against the oracle, and batched tallies
+    (fp64 and fp32-guarded) bit for bit against each problem run alone."""
+    one = [W.slab_problem(60.0, 1.0, 0.9, 4000, 6000, 2, W.SEED_HASH)]
+    t, _ = gpu_run(env, one, precision=precision)
+    c = counts_of(t, 1)[0]
+    assert int(c[0]) == 4000 == int(c[3]) + int(c[5]) + int(c[6])
+    if precision == 0:
+        o = oracle_run(oracle, one)
+        assert np.array_equal(t.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+        assert_tally_close(t.bins.cpu().numpy(), o["tally"])
+    probs, off = [], 0
+    for i, (L, nb) in enumerate([(7.0, 3), (30.0, 700), (2.5, 1), (45.0, 5000), (12.0, 64)]):
+        probs.append(W.slab_problem(L, 1.0, 0.8, 1500, nb, 2, W.SEED_HASH_HIER, tally_offset=off, key=i))
+        off += 2 * nb
+    t, _ = gpu_run(env, probs, precision=precision)
+    if precision == 0:
+        o = oracle_run(oracle, probs)
+        assert np.array_equal(t.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+        assert_tally_close(t.bins.cpu().numpy(), o["tally"])
+    bins = t.bins.cpu().numpy()
+    for p in probs:
+        alone = dict(p, tally_offset=0)
+        a, _ = gpu_run(env, [alone], n_hist_out=False, precision=precision)
+        lo, n = p["tally_offset"], 2 * p["n_bins"]
+        assert np.array_equal(a.bins.cpu().numpy()[:n], bins[lo:lo + n])
+
+
 def test_pure_absorber_beam_closed_form_on_gpu(env):
     mc, ctx, torch = env
     S, L, nb = 1.0, 4.0, 8
