@@ -135,6 +135,10 @@ struct DrawArgs {
   uint64_t* states;    // kLoad: in/out; else nullable out
   double* u;           // nullable, [draws][n]
   uint64_t* digest;    // nullable, [n]
+  // kStride digest kernel: the maps of Q T and 2 Q T steps (T = threads in
+  // the grid), the same for every thread; set by the launcher so that they
+  // stay in the parameter bank instead of registers
+  Affine half, sweep;
 };
 
 template <int M, int SEED, bool WANT_U, bool WANT_DIGEST>
@@ -206,14 +210,9 @@ __global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawA
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   if (tid >= a.n) return;
   const uint32_t draws = DRAWS > 0 ? (uint32_t)DRAWS : a.draws;
-  Affine half{1ull, 0ull}, sweep{1ull, 0ull};
   uint64_t xs = 0, seed_hash = 0;
   if constexpr (SEED == kHash) seed_hash = mcd::seed_hash_of(a.hier ? mcd::hash64(a.key, a.seed) : a.seed);
-  if constexpr (SEED == kStride) {
-    half = map_by_table(tab, a.q * nthreads);
-    sweep = map_by_table(tab, a.q * 2ull * nthreads);
-    xs = skip_by_table(tab, a.x0, a.q * (a.id_begin + tid));
-  }
+  if constexpr (SEED == kStride) xs = skip_by_table(tab, a.x0, a.q * (a.id_begin + tid));
   const uint64_t g = a.g, c = a.c;
   for (uint64_t i = tid; i < a.n; i += 2 * nthreads) {
     const uint64_t i2 = i + nthreads;
@@ -227,8 +226,8 @@ __global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawA
       x0b = mcd::hash_with(a.id_begin + (two ? i2 : i), seed_hash) & a.mask;
     } else {
       x0a = xs & a.mask;
-      x0b = mcd::apply(half, xs) & a.mask;
-      xs = mcd::apply(sweep, xs);
+      x0b = mcd::apply(a.half, xs) & a.mask;
+      xs = mcd::apply(a.sweep, xs);
     }
     uint64_t xa = x0a, xb = x0b, da = 0, db = 0;
     uint32_t sa = 0, sb = 0;
@@ -310,16 +309,22 @@ int persistent_grid(K kernel, int block, size_t smem, uint64_t work_items) {
   return (int)(want < full ? want : full);
 }
 
+template <int SEED, int DRAWS>
+void launch_digest_k(DrawArgs a, cudaStream_t s) {
+  auto k = draw_digest_m63_kernel<SEED, DRAWS>;
+  const int grid = persistent_grid(k, kDrawBlock, 0, (a.n + 1) / 2);
+  if constexpr (SEED == kStride) {
+    const uint64_t nthreads = (uint64_t)grid * kDrawBlock;
+    a.half = mcd::skip_map(a.g, a.c, a.q * nthreads);
+    a.sweep = mcd::skip_map(a.g, a.c, a.q * 2ull * nthreads);
+  }
+  k<<<grid, kDrawBlock, 0, s>>>(a);
+}
+
 template <int SEED>
 int launch_digest_m63(const DrawArgs& a, cudaStream_t s) {
-  const uint64_t work = (a.n + 1) / 2;
-  if (a.draws == 64) {
-    auto k = draw_digest_m63_kernel<SEED, 64>;
-    k<<<persistent_grid(k, kDrawBlock, 0, work), kDrawBlock, 0, s>>>(a);
-  } else {
-    auto k = draw_digest_m63_kernel<SEED, 0>;
-    k<<<persistent_grid(k, kDrawBlock, 0, work), kDrawBlock, 0, s>>>(a);
-  }
+  if (a.draws == 64) launch_digest_k<SEED, 64>(a, s);
+  else launch_digest_k<SEED, 0>(a, s);
   return mci::cuda_status(cudaGetLastError(), "draw_digest_m63_kernel launch");
 }
 
