@@ -82,7 +82,68 @@ struct RunArgs {
   uint32_t smem_slots;
   uint32_t smem_edges;  // single-problem launches: n_bins + 1 edges in shared memory (0: none)
   const double* tables; // else per-problem edge and width tables in global memory (nullable)
+  uint32_t donate_max;  // a warp with 1..donate_max live lanes after the ticket ran out donates them
+  uint32_t pool_cap;    // particles the block's shared pool holds (0: no compaction)
 };
+
+// In-block compaction of the long-chain tail.  Once the ticket runs out,
+// lanes whose histories end are no longer refilled and warps thin out (the
+// fp64 slab ran at 4 live lanes of 32).  A warp left with few live lanes
+// hands them to a shared-memory pool of its block and leaves the loop; warps
+// with dead lanes take them from the pool.  A particle carries its whole
+// state (stream, position, direction, history index, flight count), so the
+// move changes no draw and no result.  The pool is guarded by a lock taken
+// by one lane per warp, with bounded attempts; a warp that cannot take it
+// skips the hand-over (or, leaving, counts the stranded particles in
+// MC_C_DROPPED, the error the host reports).
+constexpr int kPoolWords = 9;
+struct PoolCtl {
+  int lock, n, active, pad;
+};
+
+__device__ __forceinline__ bool pool_lock(int* lk) {
+  for (int i = 0; i < (1 << 20); ++i)
+    if (atomicCAS(lk, 0, 1) == 0) {
+      __threadfence_block();
+      return true;
+    }
+  return false;
+}
+__device__ __forceinline__ void pool_unlock(int* lk) {
+  __threadfence_block();
+  atomicExch(lk, 0);
+}
+
+template <int M>
+__device__ __forceinline__ void pool_put(unsigned long long* e, const mcs::Rng<M>& r,
+                                         const mcs::SlabParticle& q, uint64_t gi, uint64_t events,
+                                         uint32_t pi) {
+  e[0] = r.x;
+  e[1] = r.draws;
+  e[2] = (unsigned long long)__double_as_longlong(q.x);
+  e[3] = (unsigned long long)__double_as_longlong(q.mu);
+  e[4] = (unsigned long long)__double_as_longlong(q.w_mu);
+  e[5] = ((unsigned long long)__float_as_uint(q.muf) << 32) | __float_as_uint(q.xf);
+  e[6] = ((unsigned long long)pi << 32) | __float_as_uint(q.wf);
+  e[7] = gi;
+  e[8] = events;
+}
+
+template <int M>
+__device__ __forceinline__ uint32_t pool_get(const unsigned long long* e, mcs::Rng<M>& r, mcs::SlabParticle& q,
+                                             uint64_t& gi, uint64_t& events) {
+  r.x = e[0];
+  r.draws = e[1];
+  q.x = __longlong_as_double((long long)e[2]);
+  q.mu = __longlong_as_double((long long)e[3]);
+  q.w_mu = __longlong_as_double((long long)e[4]);
+  q.xf = __uint_as_float((uint32_t)e[5]);
+  q.muf = __uint_as_float((uint32_t)(e[5] >> 32));
+  q.wf = __uint_as_float((uint32_t)e[6]);
+  gi = e[7];
+  events = e[8];
+  return (uint32_t)(e[6] >> 32);
+}
 
 // Per-lane counters for the lane's current problem.
 struct LaneCounts {
@@ -122,7 +183,7 @@ __device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, u
 }
 
 template <int M, bool F32, bool SMEM>
-__global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
+__global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   extern __shared__ unsigned long long s_tally[];
   __shared__ mcd::Affine tab[64];
   if (threadIdx.x == 0) {
@@ -134,6 +195,15 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
   }
   double* s_edges = a.smem_edges ? reinterpret_cast<double*>(s_tally + (SMEM ? a.smem_slots : 0u)) : nullptr;
   double* s_widths = s_edges ? s_edges + a.smem_edges : nullptr;  // n_bins widths after the edges
+  // the particle pool after the tally and the edge tables
+  unsigned long long* s_pool = s_tally + (SMEM ? a.smem_slots : 0u) + 2u * a.smem_edges;
+  __shared__ PoolCtl ctl;
+  if (threadIdx.x == 0) {
+    ctl.lock = 0;
+    ctl.n = 0;
+    ctl.active = (int)(blockDim.x >> 5);
+    ctl.pad = 0;
+  }
   if (s_edges) {
     const SlabDev& p0 = a.probs[0];
     for (uint32_t j = threadIdx.x; j + 1 < a.smem_edges; j += blockDim.x)
@@ -198,7 +268,84 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
       pool_next += min((uint64_t)__popc(dead), avail);
       dead = __ballot_sync(kFull, !alive);
     }
-    if (__ballot_sync(kFull, alive) == 0u) break;
+    if (!more && a.pool_cap != 0u) {
+      // ticket exhausted: take particles from the block's pool into dead
+      // lanes, hand this warp's few over, or leave
+      // the pool's count and active warps as lane 0 reads them: every branch
+      // below must be taken by the whole warp (full-mask shuffles inside)
+      volatile PoolCtl& vc = ctl;
+      const int hint_n = __shfl_sync(kFull, lane == 0 ? vc.n : 0, 0);
+      const int hint_active = __shfl_sync(kFull, lane == 0 ? vc.active : 0, 0);
+      if (dead != 0u && hint_n > 0) {
+        int k = 0, n = 0, ok = 0;
+        if (lane == 0) {
+          ok = pool_lock(&ctl.lock);
+          if (ok) {
+            n = vc.n;
+            k = min(n, __popc(dead));
+            vc.n = n - k;
+          }
+        }
+        k = __shfl_sync(kFull, k, 0);
+        n = __shfl_sync(kFull, n, 0);
+        if (k < 0 || n > (int)a.pool_cap || k > n) k = 0;  // never outside the pool
+        __syncwarp();
+        const unsigned rank = __popc(dead & lt_mask);
+        if (!alive && (int)rank < k) {
+          const uint32_t pi = pool_get<M>(s_pool + (size_t)(n - k + (int)rank) * kPoolWords, r, q, gi, events);
+          if ((int)pi != lc.prob) { lc.flush(a.counts); lc.prob = (int)pi; }
+          P = a.probs + pi;
+          const uint64_t id = gi - P->hist_begin;
+          sink.base = (SMEM ? s_tally : a.tally) + P->tally_offset + mcs::batch_of(id, P->n_hist, P->n_batches) * P->n_bins;
+          if (a.tables) {
+            sink.edges = a.tables + P->tab_off;
+            sink.widths = sink.edges + P->n_bins + 1;
+          }
+          alive = true;
+        }
+        __syncwarp();
+        if (lane == 0 && ok) pool_unlock(&ctl.lock);
+        dead = __ballot_sync(kFull, !alive);
+      }
+      const unsigned live = ~dead;
+      const int nlive = __popc(live);
+      if (nlive == 0 || (nlive <= (int)a.donate_max && hint_active > 1 && hint_n + nlive <= (int)a.pool_cap)) {
+        int go = 0, n = 0;
+        if (lane == 0) {
+          if (pool_lock(&ctl.lock)) {
+            n = vc.n;
+            if (nlive == 0 ? n == 0 : (vc.active > 1 && n + nlive <= (int)a.pool_cap)) {
+              vc.n = n + nlive;
+              vc.active = vc.active - 1;
+              go = 1;
+            }
+            if (!go || nlive == 0) pool_unlock(&ctl.lock);
+          } else if (nlive == 0) {
+            // cannot see the pool: leave, counting what may be stranded
+            atomicAdd(a.counts + MC_C_DROPPED, (unsigned long long)max(vc.n, 0));
+            go = 1;
+          }
+        }
+        go = __shfl_sync(kFull, go, 0);
+        n = __shfl_sync(kFull, n, 0);
+        if (go) {
+          if (nlive != 0) {
+            const uint32_t slot = (uint32_t)n + (uint32_t)__popc(live & lt_mask);
+            if (alive && slot < a.pool_cap)  // always, by the count taken under the lock
+              pool_put<M>(s_pool + (size_t)slot * kPoolWords, r, q, gi, events, (uint32_t)(P - a.probs));
+            else if (alive)
+              atomicAdd(a.counts + MC_C_DROPPED, 1ull);
+            __syncwarp();
+            if (lane == 0) pool_unlock(&ctl.lock);
+            alive = false;
+          }
+          break;
+        }
+        if (nlive == 0) continue;  // the pool holds particles: take them on the next pass
+      }
+    } else if (__ballot_sync(kFull, alive) == 0u) {
+      break;
+    }
     if (alive) {
       int outcome;
       if (events == a.event_cap) {
@@ -237,7 +384,8 @@ __global__ void __launch_bounds__(512) slab_history_kernel(const RunArgs a) {
 template <int M, bool F32, bool SMEM>
 int launch_history(const RunArgs& a, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
   auto k = slab_history_kernel<M, F32, SMEM>;
-  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u;  // edges + widths
+  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u +  // edges + widths
+                     (size_t)a.pool_cap * kPoolWords * 8u;
   if (smem > 48u * 1024u) {
     int st = mci::cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               "cudaFuncSetAttribute(slab_history_kernel)");
@@ -337,6 +485,10 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
   }
   // otherwise each problem's tables in global memory, where staged
   a.tables = a.smem_edges ? nullptr : static_cast<const double*>(L.d_tables);
+  // compaction: a warp with at most 12 live lanes hands them over; the pool
+  // holds what every other warp of the block could hand over
+  a.donate_max = 12;
+  a.pool_cap = L.block >= 64 ? (uint32_t)((L.block >> 5) - 1) * a.donate_max : 0u;
   if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
   return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
 }
