@@ -356,6 +356,7 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
   delete ctx->staged_image;
   delete ctx->fill_scratch;
   ctx->overflow.release();
+  ctx->pulse_stack.release();
   ctx->tune_tally.release();
   delete ctx->tune_cache;
   if (ctx->graphs) {
@@ -552,7 +553,16 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
       P.h_count = ctx->h_count;
     }
     const mc_pulse_spec* ps = problems[0].pulse;
-    if (ps->n_census < 2) return mci::pulse_run(P, s);
+    if (ps->n_census < 2) {
+      size_t sb = 0;
+      st = mci::pulse_stack_bytes(P, &sb);
+      if (st != MC_OK) return st;
+      st = ctx->pulse_stack.reserve(sb);
+      if (st != MC_OK) return st;
+      P.d_stack = ctx->pulse_stack.ptr;
+      P.stack_bytes = sb;
+      return mci::pulse_run(P, s);
+    }
     if (rb % ps->per_batch != 0 || re % ps->per_batch != 0) {  // (also checked by validate_run)
       mci::set_error("pulse census phases: the history range must cover whole (rep, batch) groups");
       return MC_ERR_ARG;

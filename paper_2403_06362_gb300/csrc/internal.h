@@ -71,6 +71,8 @@ struct mc_ctx {
   // Pulse problem: two generation banks of secondaries that overflowed the
   // lane stacks (hash modes).
   mci::DeviceBuf overflow;
+  // Pulse problem: the lane stacks of pending secondaries.
+  mci::DeviceBuf pulse_stack;
   // Pulse census phases: bank counts, group weight totals and two banks.
   mci::DeviceBuf census;
   // Private stream used only to capture graphs (the caller's stream may be

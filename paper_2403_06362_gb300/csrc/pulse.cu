@@ -26,9 +26,7 @@
 
 namespace {
 
-using mcp::kStack;
 using mcp::Overflow;
-using mcp::Pending;
 using mcp::PulseDev;
 using mcp::pulse_seed;
 
@@ -44,6 +42,7 @@ struct PulseArgs {
   mcd::Lcg lcg;
   uint64_t event_cap;
   uint32_t stack_depth;            // pending secondaries a lane keeps (<= kStack)
+  mcp::StackRec* stack;            // [stack_depth][threads of the launch]
   const Overflow* ovf_in;          // non-null: the work items are overflowed secondaries
   const unsigned long long* ovf_in_count;
   Overflow* ovf_out;               // non-null (hash modes): where secondaries beyond the stack go
@@ -108,7 +107,8 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt_mask = (1u << lane) - 1u;
 
-  Pending stack[kStack];
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  mcp::StackRec* const my_stack = a.stack + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t sp = 0;
   uint64_t pool_next = 0, pool_end = 0;
   bool more = true, alive = false, primary = false;
@@ -196,9 +196,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
           for (uint32_t k = 0; k + 1 < n; ++k) {
             const uint64_t seed = hash_mode ? (mcd::hash64((uint64_t)k, r.x & l.mask) & l.mask) : 0ull;
             if (sp < a.stack_depth) {
-              stack[sp].x = x;
-              stack[sp].t = t;
-              stack[sp].seed = seed;
+              mcp::stack_put(my_stack + sp * nthreads, x, t, seed);
               ++sp;
               ++lc.children;
             } else if (a.ovf_out) {  // hash modes only
@@ -237,10 +235,10 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
       events = 0;
       if (sp > 0) {  // the next secondary of the family; its direction below
         --sp;
-        x = stack[sp].x;
-        t = stack[sp].t;
+        uint64_t seed;
+        mcp::stack_get(my_stack + sp * nthreads, x, t, seed);
         if constexpr (HASH) {
-          r = mcs::Rng<M>{stack[sp].seed, 0ull};
+          r = mcs::Rng<M>{seed, 0ull};
           mu = mcx::two_u_minus_1(r.next_n(l));
         } else {
           redraw = true;
@@ -300,6 +298,28 @@ int pulse_prep(void* d_prob, cudaStream_t s) {
   return cuda_status(cudaGetLastError(), "pulse_prep_kernel launch");
 }
 
+// The largest grid pulse_run launches for L (one persistent block per slot).
+static int pulse_full_grid(const PulseLaunch& L, uint64_t* full_out) {
+  const bool hash = L.seeding != MC_SEED_STRIDE;
+  auto k = L.lcg.m == 63 ? (hash ? pulse_kernel<63, true> : pulse_kernel<63, false>)
+                         : (hash ? pulse_kernel<0, true> : pulse_kernel<0, false>);
+  int per_sm = 0;
+  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
+                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");
+  if (st != MC_OK) return st;
+  if (per_sm < 1) per_sm = 1;
+  *full_out = (uint64_t)L.num_sms * per_sm;
+  return MC_OK;
+}
+
+int pulse_stack_bytes(const PulseLaunch& L, size_t* bytes) {
+  uint64_t full = 0;
+  const int st = pulse_full_grid(L, &full);
+  if (st != MC_OK) return st;
+  *bytes = (size_t)full * (size_t)L.block * L.stack_depth * sizeof(mcp::StackRec);
+  return MC_OK;
+}
+
 int pulse_run(const PulseLaunch& L, cudaStream_t s) {
   PulseArgs a{};
   a.prob = static_cast<const PulseDev*>(L.d_prob);
@@ -314,15 +334,17 @@ int pulse_run(const PulseLaunch& L, cudaStream_t s) {
   a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
   a.event_cap = L.event_cap;
   a.stack_depth = L.stack_depth;
+  a.stack = static_cast<mcp::StackRec*>(L.d_stack);
   const bool hash = L.seeding != MC_SEED_STRIDE;
   auto k = L.lcg.m == 63 ? (hash ? pulse_kernel<63, true> : pulse_kernel<63, false>)
                          : (hash ? pulse_kernel<0, true> : pulse_kernel<0, false>);
-  int per_sm = 0;
-  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
-                       "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");
+  uint64_t full = 0;
+  int st = pulse_full_grid(L, &full);
   if (st != MC_OK) return st;
-  if (per_sm < 1) per_sm = 1;
-  const uint64_t full = (uint64_t)L.num_sms * per_sm;
+  if (!L.d_stack || L.stack_bytes < (size_t)full * L.block * L.stack_depth * sizeof(mcp::StackRec)) {
+    set_error("pulse transport: the lane stacks need more device memory than was given");
+    return MC_ERR_ARG;
+  }
   const uint64_t warps_needed = (a.total + a.chunk - 1) / a.chunk;
   const uint64_t blocks_needed = (warps_needed * 32 + L.block - 1) / L.block;
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(full, blocks_needed));

@@ -24,12 +24,33 @@ struct PulseDev {
   uint32_t nu_floor, pad2;
 };
 
-constexpr int kStack = 256;
+constexpr int kStack = 256;  // most pending secondaries a lane keeps (run config stack_depth)
 
+// A pending secondary on a lane's local stack (census phases: shallow
+// families, where the L1-resident local stack measured faster).
 struct Pending {
   double x, t;
   uint64_t seed;
 };
+
+// A pending secondary in device memory (one 32-byte sector): the stacks of
+// all lanes of a launch, depth-major (entry j of every lane together), so a
+// push writes one whole sector and the shallow entries, the busy ones, stay
+// together in L2.
+struct __align__(32) StackRec {
+  double x, t;
+  uint64_t seed, pad;
+};
+__device__ __forceinline__ void stack_put(StackRec* e, double x, double t, uint64_t seed) {
+  reinterpret_cast<double2*>(e)[0] = make_double2(x, t);
+  reinterpret_cast<ulonglong2*>(e)[1] = make_ulonglong2(seed, 0ull);
+}
+__device__ __forceinline__ void stack_get(const StackRec* e, double& x, double& t, uint64_t& seed) {
+  const double2 v = reinterpret_cast<const double2*>(e)[0];
+  x = v.x;
+  t = v.y;
+  seed = reinterpret_cast<const ulonglong2*>(e)[1].x;
+}
 
 // A hash-seeded secondary that did not fit on its lane's stack (32 bytes):
 // it waits in a device bank for a later launch of the same phase.

@@ -82,6 +82,9 @@ struct PulseLaunch {
   int block, num_sms;
   uint32_t seeding;              // MC_SEED_*: selects the kernel variant
   uint32_t stack_depth;          // 1..256
+  // Lane stacks of pending secondaries: pulse_stack_bytes(...) bytes.
+  void* d_stack;
+  size_t stack_bytes;
   // Overflow bank (hash modes; pulse_ovf_bytes(ovf_cap) bytes; nullptr: a
   // full stack drops, MC_ERR_CAPACITY) and a pinned count for the host loop.
   void* d_ovf;
@@ -94,6 +97,7 @@ size_t pulse_dev_size();
 int pulse_fill_host(const mc_problem* src, void* dst);
 int pulse_prep(void* d_prob, cudaStream_t s);
 int pulse_run(const PulseLaunch& L, cudaStream_t s);
+int pulse_stack_bytes(const PulseLaunch& L, size_t* bytes);
 
 // Census phases with population control (pulse_census.cu).  d_buf holds
 // pulse_census_bytes(groups, cap) bytes; the histories of `base` cover
