@@ -506,9 +506,20 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             n = p[0]["n_histories"]
             for prec in (0, 1):
                 ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, precision=prec)
-                res[f"{name}_{sname}_{'fp32' if prec else 'fp64'}"] = entry(ms, tally, cp, n)
+                e = entry(ms, tally, cp, n)
                 if prec == 0:
                     hist_bins = tally.bins.clone()
+                    r64 = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
+                else:
+                    # fp32-guarded flux against the fp64 flux, per bin: relative
+                    # difference and the difference in fp64 standard errors
+                    r32 = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
+                    d = np.abs(r32.flux - r64.flux)
+                    f64 = np.abs(r64.flux)
+                    se = r64.rel_err * f64
+                    e["fp32_vs_fp64_rel_diff_max"] = float(np.max(np.where(f64 > 0, d / np.where(f64 > 0, f64, 1), 0)))
+                    e["fp32_vs_fp64_diff_in_se_max"] = float(np.max(np.where(se > 0, d / np.where(se > 0, se, 1), 0)))
+                res[f"{name}_{sname}_{'fp32' if prec else 'fp64'}"] = e
             ms, tally, cp = timed(p, reps=1, precision=0, schedule=1, use_graph=1)
             e = entry(ms, tally, cp, n)
             e["bits_identical_to_history"] = bool(torch.equal(tally.bins, hist_bins))
@@ -539,10 +550,27 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
     # 256 batched slab problems
     probs = W.slab_batched(W.SEED_HASH_HIER)
     nh = sum(p["n_histories"] for p in probs)
-    ms32, _, _ = timed(probs, reps=2, precision=1)
+    ms32, t32, _ = timed(probs, reps=2, precision=1)
     ms32g, _, _ = timed(probs, reps=2, precision=1, use_graph=1)
     ms32a, _, _ = timed(probs, reps=2, precision=1, schedule=2)
-    ms64, _, _ = timed(probs, reps=1, precision=0)
+    ms64, t64, _ = timed(probs, reps=1, precision=0)
+    # fp32-guarded against fp64: per-bin relative difference of the tallies
+    # and the histories whose final stream state differs (a decision that went
+    # the other way), from one untimed run of each with per-history outputs
+    g32 = t32.bins.cpu().numpy().astype(np.float64)
+    g64 = t64.bins.cpu().numpy().astype(np.float64)
+    nzb = g64 != 0
+    rel = np.abs(g32[nzb] - g64[nzb]) / np.abs(g64[nzb])
+    cp_h = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    hs = {}
+    for prec in (0, 1):
+        th = mc.Tally(W.tally_slots(probs), len(probs), n_histories=nh)
+        mc.mc_transport_run(ctx, lcg, cp_h, mc.mc_run_config(precision=prec), th.c, stream)
+        torch.cuda.synchronize()
+        hs[prec] = th.hist_state.cpu().numpy()
+        del th
+    diverged = int(np.count_nonzero(hs[0] != hs[1]))
+    del hs
     singles = []
     for p in probs:
         q = dict(p)
@@ -561,7 +589,10 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                            "ms_batched_fp32_autotuned": ms32a, "ms_batched_fp64": ms64,
                            "ms_single_fp64_loop": ms_single,
                            "histories_per_s_batched_fp32": nh / (best32 / 1e3),
-                           "speedup_batched_fp32_over_single_fp64": ms_single / best32}
+                           "speedup_batched_fp32_over_single_fp64": ms_single / best32,
+                           "fp32_vs_fp64_bin_rel_diff": {"max": float(rel.max()), "median": float(np.median(rel)),
+                                                         "bins": int(rel.size)},
+                           "fp32_histories_diverged": diverged}
 
     # Section 5 experiment: 30 repetitions x 1000 batches x 1000 sources, hash
     # (hierarchical seeds) vs stride; Shapiro-Wilk on each of the 20 points
