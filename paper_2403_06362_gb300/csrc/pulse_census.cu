@@ -70,6 +70,7 @@ struct CensusArgs {
   uint64_t range_begin, n_src;  // first phase: source histories
   uint64_t group_begin;         // first group of the range
   const BankRec* in;            // later phases: banked particles
+  int stage;                    // bank items staged per chunk in shared memory (chunk <= kPrefetch)
   const unsigned long long* in_count;
   const GroupCtl* ctl;          // per group: control of `in`
   BankRec* out;
@@ -114,8 +115,20 @@ struct CensusCounts {
   }
 };
 
+// Bank items arrive one lane at a time as lanes finish, and each start is
+// two dependent loads (the record, then its group's control).  A warp that
+// takes a chunk of bank items loads all of its records and their controls
+// at once into shared memory (at most kPrefetch items per warp), so the
+// chunk pays one round trip instead of one per item.
+constexpr uint32_t kPrefetch = 64;  // largest chunk staged
+struct StagedItem {
+  BankRec e;
+  GroupCtl gc;
+};
+
 template <int M>
-__global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
+__global__ void __maxnreg__(96) pulse_census_kernel(const CensusArgs a) {
+  extern __shared__ StagedItem s_items[];
   __shared__ PulseDev sP;
   if (threadIdx.x == 0) sP = *a.prob;
   __syncthreads();
@@ -126,6 +139,8 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
   const unsigned lt_mask = (1u << lane) - 1u;
   const uint64_t total = a.ovf_in ? min((uint64_t)*a.ovf_in_count, a.ovf_cap)
                                   : (a.in ? min((uint64_t)*a.in_count, a.cap) : a.n_src);
+  const bool staged = a.stage && a.in != nullptr && a.ovf_in == nullptr;
+  uint64_t chunk_base = 0;
 
   Pending stack[kStack];
   uint32_t sp = 0;
@@ -150,6 +165,17 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
         if (b0 >= total) { more = false; break; }
         pool_next = b0;
         pool_end = min((uint64_t)b0 + (uint64_t)a.chunk, total);
+        chunk_base = b0;
+        if (staged) {
+          // the chunk's records and their group controls, coalesced
+          StagedItem* w = s_items + (threadIdx.x >> 5) * a.chunk;
+          for (uint64_t j = lane; b0 + j < pool_end; j += 32) {
+            const BankRec e = a.in[b0 + j];
+            w[j].e = e;
+            w[j].gc = a.ctl[e.group - a.group_begin];
+          }
+          __syncwarp();
+        }
       }
       const uint64_t avail = pool_end - pool_next;
       const unsigned rank = __popc(dead & lt_mask);
@@ -189,9 +215,10 @@ __global__ void __launch_bounds__(256) pulse_census_kernel(const CensusArgs a) {
           ++lc.src;
           alive = true;
         } else {
-          const BankRec e = a.in[item];
+          const StagedItem* si = staged ? s_items + (threadIdx.x >> 5) * a.chunk + (item - chunk_base) : nullptr;
+          const BankRec e = staged ? si->e : a.in[item];
           grp = e.group;
-          const GroupCtl gc = a.ctl[grp - a.group_begin];
+          const GroupCtl gc = staged ? si->gc : a.ctl[grp - a.group_begin];
           const double xi = (double)(mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11) * 0x1p-53;
           const uint64_t n = (uint64_t)floor(e.w * gc.ratio + xi);
           if (n == 0) {
@@ -384,8 +411,10 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   BankRec* bank[2] = {reinterpret_cast<BankRec*>(base + off),
                       reinterpret_cast<BankRec*>(base + off + align256(L.cap * sizeof(BankRec)))};
   auto k = L.base.lcg.m == 63 ? pulse_census_kernel<63> : pulse_census_kernel<0>;
+  const int stage = L.base.chunk <= kPrefetch ? 1 : 0;
+  const size_t stage_smem = stage ? (size_t)(L.base.block / 32) * L.base.chunk * sizeof(StagedItem) : 0u;
   int per_sm = 0;
-  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.base.block, 0),
+  int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.base.block, stage_smem),
                        "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse census)");
   if (st != MC_OK) return st;
   if (per_sm < 1) per_sm = 1;
@@ -404,6 +433,7 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   a.lcg = mcd::Lcg{L.base.lcg.g, L.base.lcg.c, mcd::mask_of(L.base.lcg.m), L.base.lcg.m};
   a.event_cap = L.base.event_cap;
   a.stack_depth = L.base.stack_depth;
+  a.stage = stage;
   auto* ocnt = static_cast<unsigned long long*>(L.base.d_ovf);
   Overflow* obank[2] = {
       reinterpret_cast<Overflow*>(static_cast<char*>(L.base.d_ovf) + 256),
@@ -434,7 +464,7 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
     a.ovf_out = obank[0];
     a.ovf_out_count = ocnt;
     MC_TRY_CUDA(cudaMemsetAsync(ocnt, 0, 2 * sizeof(unsigned long long), s));
-    k<<<(int)grid, L.base.block, 0, s>>>(a);
+    k<<<(int)grid, L.base.block, p == 1 ? 0u : stage_smem, s>>>(a);
     st = cuda_status(cudaGetLastError(), "pulse_census_kernel launch");
     if (st != MC_OK) return st;
     // secondaries that overflowed the lane stacks, generation by generation
