@@ -80,8 +80,10 @@ def test_census_group_ranges_add_up(env, oracle):
     assert np.array_equal(np.delete(counts_of(t), skip), np.delete(counts_of(whole), skip))
 
 
-@pytest.mark.parametrize("block,chunk", [(64, 1), (256, 64)])
+@pytest.mark.parametrize("block,chunk", [(64, 1), (256, 64), (128, 128)])
 def test_census_bits_independent_of_launch_shape(env, block, chunk):
+    # chunks of up to 64 bank items are staged in shared memory, larger ones
+    # are read item by item: both give the default launch's bits
     a = W.azurv1(n_reps=1, n_batches=40, per_batch=1000, n_census=10)
     base = run_gpu(env, a)
     t = run_gpu(env, a, block=block, chunk=chunk)
