@@ -14,6 +14,8 @@
 // integer instructions.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <cstdint>
 
 #include "internal.h"
@@ -296,15 +298,19 @@ __global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawA
 // blocks than the work needs.
 template <typename K>
 int persistent_grid(K kernel, int block, size_t smem, uint64_t work_items) {
-  static int cached_sms = 0;
+  static std::atomic<int> cached[64];  // SM count per device ordinal (0: not read yet)
   int dev = 0;
   cudaGetDevice(&dev);
-  if (cached_sms == 0) cudaDeviceGetAttribute(&cached_sms, cudaDevAttrMultiProcessorCount, dev);
+  int sms = dev >= 0 && dev < 64 ? cached[dev].load(std::memory_order_relaxed) : 0;
+  if (sms == 0) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dev >= 0 && dev < 64) cached[dev].store(sms, std::memory_order_relaxed);
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
   if (per_sm < 1) per_sm = 1;
   uint64_t want = (work_items + block - 1) / block;
-  uint64_t full = (uint64_t)cached_sms * per_sm;
+  uint64_t full = (uint64_t)sms * per_sm;
   if (want < 1) want = 1;
   return (int)(want < full ? want : full);
 }
