@@ -15,7 +15,6 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
-
 #include <cstdint>
 
 #include "internal.h"
