@@ -424,7 +424,8 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   L.lcg = *lcg;
   L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 40);
   const uint64_t smem_cap = 8192;  // slots (64 KiB) staged in shared memory under "auto"
-  const bool fits = tally->n_slots * 8u <= ctx->smem_optin;
+  // (2 KiB left for the kernel's own static shared memory)
+  const bool fits = tally->n_slots * 8u + 2048u <= ctx->smem_optin;
   if (cfg->tally_mode == 1 && !fits) {
     mci::set_error("mc_transport_run: %llu tally slots do not fit in shared memory",
                    (unsigned long long)tally->n_slots);

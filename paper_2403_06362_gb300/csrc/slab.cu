@@ -382,11 +382,34 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
 }
 
 template <int M, bool F32, bool SMEM>
-int launch_history(const RunArgs& a, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
+int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
   auto k = slab_history_kernel<M, F32, SMEM>;
-  const size_t smem = (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u +  // edges + widths
-                     (size_t)a.pool_cap * kPoolWords * 8u;
-  if (smem > 48u * 1024u) {
+  RunArgs a = a0;
+  // Static shared memory of this instantiation (read once) and the device's
+  // opt-in limit: what does not fit beside them is given up, the compaction
+  // pool first and then the edge tables (both only save time).
+  static size_t static_smem = ~(size_t)0;
+  if (static_smem == ~(size_t)0) {
+    cudaFuncAttributes fa{};
+    const int st = mci::cuda_status(cudaFuncGetAttributes(&fa, k), "cudaFuncGetAttributes(slab_history_kernel)");
+    if (st != MC_OK) return st;
+    static_smem = fa.sharedSizeBytes;
+  }
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  auto dynamic_smem = [&a]() {
+    return (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u +  // edges + widths
+           (size_t)a.pool_cap * kPoolWords * 8u;
+  };
+  if (static_smem + dynamic_smem() > (size_t)optin) a.pool_cap = 0;
+  if (static_smem + dynamic_smem() > (size_t)optin) a.smem_edges = 0;
+  const size_t smem = dynamic_smem();
+  if (static_smem + smem > (size_t)optin) {
+    mci::set_error("slab_history_kernel: %u tally slots do not fit in shared memory", a.smem_slots);
+    return MC_ERR_ARG;
+  }
+  if (static_smem + smem > 48u * 1024u) {
     int st = mci::cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                               "cudaFuncSetAttribute(slab_history_kernel)");
     if (st != MC_OK) return st;

@@ -99,6 +99,19 @@ def test_tally_bits_independent_of_launch_shape(env, oracle, block, chunk, mode)
     assert np.array_equal(counts_of(t, 1), counts_of(base, 1))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_large_blocks_with_staged_tally_and_pool(env, precision):
+    """512-thread blocks with a 4000-slot shared-memory tally, the edge
+    tables and the compaction pool: over 48 KiB of shared memory with the
+    kernel's static part; the bits equal the default launch's."""
+    probs = W.slab_long(W.SEED_HASH, n_histories=20_000)
+    base, _ = gpu_run(env, probs, n_hist_out=False, precision=precision)
+    for block in (512, 128):
+        t, _ = gpu_run(env, probs, n_hist_out=False, precision=precision, block=block)
+        assert np.array_equal(t.bins.cpu().numpy(), base.bins.cpu().numpy())
+        assert np.array_equal(counts_of(t, 1), counts_of(base, 1))
+
+
 def test_ranges_accumulate_to_the_same_bits(env):
     mc, ctx, torch = env
     probs = W.slab_small(W.SEED_STRIDE, n_histories=20_000)
