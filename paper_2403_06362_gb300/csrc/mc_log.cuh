@@ -8,12 +8,12 @@
 // reduction of P. T. P. Tang, "Table-driven implementation of the logarithm
 // function in IEEE floating-point arithmetic", ACM TOMS 16(4), 1990.  With
 // x = 1 - u = K 2^-53 (K = 2^53 - n, exact) = 2^e m, m in [1, 2), and
-// F = 1 + (2j+1)/256 the midpoint of m's cell among 128 equal cells,
-//   ln x = e ln 2 + ln F + ln(1 + r),  r = (m - F) / F,  |r| < 2^-8,
-// where m - F is an exact integer difference, r is formed with a 64-bit
-// reciprocal of F (scale 2^71), ln(1 + r) comes from its series through r^8
-// by Horner's rule on 64-bit signed fixed point (scale 2^62; the terms from
-// r^5 on, below 2^-42, on 32 bits), and the sum is
+// F = 1 + j/1024 the left end of m's cell among 1024 equal cells,
+//   ln x = e ln 2 + ln F + ln(1 + r),  r = (m - F) / F,  0 <= r < 2^-10,
+// where m - F is the exact low 42 bits of m's mantissa, r is formed with a
+// 64-bit reciprocal of F (scale 2^73), ln(1 + r) comes from its series
+// through r^6 by Horner's rule on non-negative fixed point (the inner terms
+// on 32 bits, the outer two on 64), and the sum is
 // accumulated on 128 bits with scale 2^90 (ln 2 and ln F from 128-bit
 // tables).  For u < 2^-8 (x so close to 1 that e ln 2 + ln F would cancel)
 // -ln(1 - u) = u (1 + u/2 + ... + u^8/9) is used instead, relative to u.
@@ -118,6 +118,14 @@ __host__ __device__ __forceinline__ int mulhi32_(int a, int b) {
 #endif
 }
 
+__host__ __device__ __forceinline__ uint32_t umulhi32_(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
 __host__ __device__ __forceinline__ W128 neg128(W128 a) {
   W128 r;
   r.lo = 0ull - a.lo;
@@ -155,13 +163,29 @@ __host__ __device__ __forceinline__ double w128_to_double(W128 a, int scale) {
   return from_bits(((biased - 1ull) << 52) + m53);  // the leading 1 adds one to the exponent
 }
 
-// The same for 2^82 <= a < 2^96 (the leading 1 at bit 82..95 of the high
-// word's range), without branches.
+// The same for 2^82 <= a < 2^96, on the three low 32-bit words (the high
+// word is below 2^32), without branches.
+__host__ __device__ __forceinline__ uint32_t clz32_(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return (uint32_t)__clz((int)x);
+#else
+  return x ? (uint32_t)__builtin_clz(x) : 32u;
+#endif
+}
+// The low word of (hi:lo) >> s, 0 <= s <= 32.
+__host__ __device__ __forceinline__ uint32_t fsr32_(uint32_t lo, uint32_t hi, uint32_t s) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_rc(lo, hi, s);
+#else
+  return (uint32_t)((((uint64_t)hi << 32) | lo) >> s);
+#endif
+}
 __host__ __device__ __forceinline__ double w128_to_double_hi(W128 a, int scale) {
-  const int top = 127 - clz64_(a.hi);  // 82..95
-  const int sh = top - 63;             // 19..32
-  const uint64_t m64 = (a.hi << (64 - sh)) | (a.lo >> sh);
-  const bool sticky = (a.lo << (64 - sh)) != 0ull;
+  const uint32_t h = (uint32_t)a.hi, l1 = (uint32_t)(a.lo >> 32), l0 = (uint32_t)a.lo;
+  const int top = 95 - (int)clz32_(h);  // 82..95
+  const uint32_t sh = (uint32_t)(top - 63);  // 19..32
+  const uint64_t m64 = ((uint64_t)fsr32_(l1, h, sh) << 32) | fsr32_(l0, l1, sh);  // bits sh..sh+63
+  const bool sticky = (l0 << (32u - sh)) != 0u;  // any of the bits below sh
   uint64_t m53 = m64 >> 11;
   const uint64_t rest = m64 & 0x7FFull;
   if (rest > 0x400ull || (rest == 0x400ull && (sticky || (m53 & 1ull)))) ++m53;
@@ -192,29 +216,23 @@ __host__ __device__ __forceinline__ double log1m_n(uint64_t n) {
   const int lz = clz64_(K);             // 12..63
   const int e = 10 - lz;                // x = 2^e m
   const uint64_t mant = K << (lz - 11);  // m 2^52, leading 1 at bit 52
-  const int j = (int)((mant >> 45) & 127ull);
-  const long long D = (long long)mant - (long long)((1ull << 52) + ((uint64_t)(2 * j + 1) << 44));  // (m - F) 2^52
-  const uint64_t inv = MC_LOG_LD(kInvF, j);                                                        // 2^64 / F
-  const uint64_t ad = D < 0 ? (uint64_t)(-D) : (uint64_t)D;
-  const uint64_t pr = (umulhi_(ad, inv) << 19) | ((ad * inv) >> 45);  // |r| 2^71
-  const long long R = D < 0 ? -(long long)pr : (long long)pr;
-  // ln(1 + r) = r (1 + r (c2 + r (c3 + r (c4 + r Q)))), Q = c5 + r (c6 + r (c7 + r c8)):
-  // |r^5 Q| < 2^-42, so Q needs only 32-bit arithmetic (scale 2^30, r at 2^39)
-  const int R32 = (int)(R >> 32);
-  int q = (int)(kLn1pC[7] >> 32);
-  q = (int)(kLn1pC[6] >> 32) + (mulhi32_(R32, q) >> 7);
-  q = (int)(kLn1pC[5] >> 32) + (mulhi32_(R32, q) >> 7);
-  q = (int)(kLn1pC[4] >> 32) + (mulhi32_(R32, q) >> 7);
-  long long t = (long long)q << 32;  // scale 2^62
-#pragma unroll
-  for (int k = 3; k >= 0; --k) t = kLn1pC[k] + (smulhi_(R, t) >> 7);
-  // ln(1 + r) 2^71 = (R t) >> 62, then to scale 2^90 (sign-extended)
-  const long long ph = smulhi_(R, t);
-  const uint64_t pl = (uint64_t)R * (uint64_t)t;
-  const long long p71 = (long long)(((uint64_t)ph << 2) | (pl >> 62));
+  const int j = (int)((mant >> 42) & (uint64_t)(kLogCells - 1));  // m in [F_j, F_j + 2^-10)
+  const uint64_t D = mant & ((1ull << 42) - 1ull);                // (m - F_j) 2^52, exact
+  const uint64_t R = umulhi_(D << 22, MC_LOG_LD(kInvF, j));       // r 2^73 (2^63 / F_j in the table)
+  // ln(1 + r) = r P, P = 1 - r Q0, Q0 = 1/2 - r Q1, Q1 = 1/3 - r Q2, Q2 = 1/4 - r Q3,
+  // Q3 = 1/5 - r/6 (the r^7 term is below 2^-72): r and Q3, Q2 and Q1 - 85/256
+  // on 32 bits, Q0 and P on 64 (scale 2^63); every quantity is non-negative.
+  const uint32_t r32 = (uint32_t)(R >> 31);                        // r 2^42
+  uint32_t q = kQ3 - (umulhi32_(r32, kQ4) >> 10);                  // Q3 2^32
+  q = (1u << 30) - (umulhi32_(r32, q) >> 10);                      // Q2 2^32
+  q = kQ1B - (umulhi32_(r32, q) >> 1);                             // (Q1 - 85/256) 2^41
+  const uint64_t rq = ((uint64_t)(uint32_t)(R >> 32) * q + (((uint64_t)(uint32_t)R * q) >> 32)) >> 19;
+  const uint64_t q0 = (1ull << 62) - (((R >> 10) * 85ull) >> 8) - rq;  // Q0 2^63
+  const uint64_t P = (1ull << 63) - (umulhi_(R, q0) >> 9);            // P 2^63
+  const uint64_t p72 = umulhi_(R, P);                                 // ln(1 + r) 2^72
   W128 p;
-  p.lo = (uint64_t)p71 << 19;
-  p.hi = (uint64_t)(p71 >> 45);
+  p.lo = p72 << 18;
+  p.hi = p72 >> 46;
   // -ln x = |e| ln 2 - ln F - ln(1 + r) > 2^-8, on 128 bits with scale 2^90
   const uint64_t ae = (uint64_t)(-e);
   W128 a;
