@@ -77,47 +77,34 @@ __host__ __device__ __forceinline__ bool abs_le(double x, double h) {
   return (to_bits(x) & ~(1ull << 63)) <= to_bits(h);
 }
 
-// q = floor(2^105 / M) for 2^52 < M < 2^53, and the rounding of the exact
-// quotient to nearest (ties cannot occur: 2^106 = (2q + 1) M would make M a
-// power of two).  An fp32 reciprocal gives 22 bits; one Newton step on
-// 128-bit products and one on 64-bit remainders bring q within a few
-// units; an exact remainder fixes the last ones.
+// q = RN(2^105 / M) for 2^52 < M < 2^53 (ties cannot occur: 2^106 = (2q + 1) M
+// would make M a power of two).  With m = M 2^-52 = F (1 + r), F = 1 + j/1024
+// the left end of m's cell (the table of 2^63 / F that the logarithm uses)
+// and 0 <= r < 2^-10,
+//   2^53 / m = (2^53 / F) (1 - r (1 - r (1 - r (1 - r (1 - r))))) + O(r^6 < 2^-60)
+// by Horner's rule on non-negative fixed point (the inner terms on 32 bits)
+// puts q within a unit; an exact remainder fixes it and rounds.
 __host__ __device__ __forceinline__ uint64_t recip_mantissa(uint64_t M) {
-  // 1. q0 ~ 2^105 / M from rf = RN(1 / (M >> 29)) ~ 2^29 / M
-  const uint32_t mh = (uint32_t)(M >> 29);  // [2^23, 2^24): exact in fp32
-  float rf = rcp_f32((float)mh);
-  uint32_t rb;
+  const int j = (int)((M >> 42) & 1023ull);
 #ifdef __CUDA_ARCH__
-  rb = __float_as_uint(rf);
+  const uint64_t inv = __ldg(&mclog::dev::kInvF[j]);  // 2^63 / F
 #else
-  std::memcpy(&rb, &rf, sizeof rb);
+  const uint64_t inv = mclog::host::kInvF[j];
 #endif
-  const int er = (int)(rb >> 23) - 127;             // -24 or -23
-  const uint64_t mr = (uint64_t)((rb & 0x7FFFFFu) | 0x800000u);
-  uint64_t q = mr << (er + 53);                      // rf * 2^76, within 2^31 of 2^105 / M
-  // 2. e = 2^105 - q M on 128 bits; q += e q / 2^105 with e and q truncated
-  {
-    const uint64_t lo = q * M, hi = mulhi64(q, M);   // q M < 2^107
-    // e = (2^41 : 0) - (hi : lo)
-    const uint64_t elo = 0ull - lo;
-    const uint64_t ehi = (1ull << 41) - hi - (lo != 0ull ? 1ull : 0ull);
-    const long long es = (long long)((ehi << 12) | (elo >> 52));  // e >> 52, |es| < 2^32
-    const long long qs = (long long)(q >> 23);                      // < 2^31
-    const long long d = (es * qs) >> 30;                            // ~ e / M
-    q = (uint64_t)((long long)q + d);
-  }
-  // 3. e1 = 2^105 - q M fits in 64 signed bits now (|e1| < 2^62)
-  {
-    const long long e1 = (long long)(0ull - q * M);
-    const uint64_t ea = e1 < 0 ? (uint64_t)(-e1) : (uint64_t)e1;
-    const uint64_t d = mulhi64(ea, q) >> 41;  // ~ |e1| / M
-    q = e1 < 0 ? q - d : q + d;
-  }
-  // 4. exact remainder r = 2^105 - q M, 0 <= r < M, then round
-  long long r = (long long)(0ull - q * M);
-  for (int i = 0; i < 4 && r < 0; ++i) { --q; r += (long long)M; }
-  for (int i = 0; i < 4 && r >= (long long)M; ++i) { ++q; r -= (long long)M; }
-  if ((uint64_t)r * 2ull > M) ++q;
+  const uint64_t R = mclog::umulhi_((M & ((1ull << 42) - 1ull)) << 22, inv);  // r 2^73
+  const uint32_t r32 = (uint32_t)(R >> 31);                                     // r 2^42
+  uint32_t t = (1u << 31) - (r32 >> 11);                       // T3 = 1 - r, scale 2^31
+  t = (1u << 31) - (mclog::umulhi32_(r32, t) >> 10);           // T2 = 1 - r T3, scale 2^31
+  t = (1u << 31) - mclog::umulhi32_(r32, t);                   // T1 - (1 - 2^-10), scale 2^41
+  const uint64_t rt = ((uint64_t)(uint32_t)(R >> 32) * t + (((uint64_t)(uint32_t)R * t) >> 32)) >> 19;
+  const uint64_t t0 = (1ull << 63) - ((R >> 10) - (R >> 20)) - rt;         // T0 = 1 - r T1, scale 2^63
+  const uint64_t S = (1ull << 63) - (mclog::umulhi_(R, t0) >> 9);          // 1 / (1 + r), scale 2^63
+  uint64_t q = mclog::umulhi_(inv, S) >> 9;                                // ~ 2^53 / m
+  // exact remainder r = 2^105 - q M (|r| < 2^63: the low words decide), then round
+  long long rem = (long long)(0ull - q * M);
+  for (int i = 0; i < 4 && rem < 0; ++i) { --q; rem += (long long)M; }
+  for (int i = 0; i < 4 && rem >= (long long)M; ++i) { ++q; rem -= (long long)M; }
+  if ((uint64_t)rem * 2ull > M) ++q;
   return q;
 }
 
