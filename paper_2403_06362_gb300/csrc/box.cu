@@ -101,6 +101,36 @@ struct BoxCounts {
     if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
     clear();
   }
+  // The same for a whole converged warp: sums first, then one lane's atomics
+  // (a problem's counters share a cache line).
+  __device__ void flush_warp(unsigned long long* counts) {
+    const int p = mcd::warp_common_prob(prob);
+    if (p == -2) { flush(counts); return; }
+    if (p < 0) return;
+    const unsigned long long so = mcd::warp_sum64(src), fl = mcd::warp_sum64(flights), co = mcd::warp_sum64(coll),
+                             le = mcd::warp_sum64(leaks), ki = mcd::warp_sum64(kills), sp = mcd::warp_sum64(splits),
+                             ch = mcd::warp_sum64(children), cp = mcd::warp_sum64(capped), ex = mcd::warp_sum64(exh),
+                             dr = mcd::warp_sum64(draws), ed = mcd::warp_sum64(exd), mx = mcd::warp_max64(maxd);
+    if ((threadIdx.x & 31u) == 0u) {
+      unsigned long long* c = counts + (size_t)p * MC_NCOUNT;
+      if (so) atomicAdd(c + MC_C_SOURCE, so);
+      if (fl) atomicAdd(c + MC_C_FLIGHTS, fl);
+      if (co) {
+        atomicAdd(c + MC_C_COLLISIONS, co);
+        atomicAdd(c + MC_C_SCATTERS, co);
+      }
+      if (le) atomicAdd(c + MC_C_LEAK_HI, le);
+      if (ki) atomicAdd(c + MC_C_ROULETTE_KILLS, ki);
+      if (sp) atomicAdd(c + MC_C_SPLITS, sp);
+      if (ch) atomicAdd(c + MC_C_CHILDREN, ch);
+      if (cp) atomicAdd(c + MC_C_CAPPED, cp);
+      if (ex) atomicAdd(c + MC_C_EXCEED_HIST, ex);
+      if (dr) atomicAdd(c + MC_C_DRAWS, dr);
+      if (ed) atomicAdd(c + MC_C_EXCEED_DRAWS, ed);
+      if (mx) atomicMax(c + MC_C_MAX_DRAWS, mx);
+    }
+    clear();
+  }
 };
 
 __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64_t gi) {
@@ -243,7 +273,7 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
       if (lc.draws > (1ull << 31)) lc.flush(a.counts);
     }
   }
-  lc.flush(a.counts);
+  lc.flush_warp(a.counts);
 }
 
 }  // namespace

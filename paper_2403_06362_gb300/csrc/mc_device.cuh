@@ -161,4 +161,26 @@ __device__ __forceinline__ double u01(uint64_t x, uint32_t m) {
 
 __device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
 
+// Warp-level aggregation of per-lane counters before their global atomics:
+// a run's counters for one problem share a cache line, so one atomic per lane
+// and counter would all queue at the same L2 slice.  Called by a full,
+// converged warp.
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+// The problem index all lanes with counts share: -1 when no lane has counts,
+// -2 when lanes hold counts of different problems.
+__device__ __forceinline__ int warp_common_prob(int prob) {
+  const int p = __reduce_max_sync(0xffffffffu, prob);
+  return __any_sync(0xffffffffu, prob >= 0 && prob != p) ? -2 : p;
+}
+
 }  // namespace mcd

@@ -88,6 +88,24 @@ struct PulseCounts {
     if (exd) atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)exd);
     if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
   }
+  // The same for a whole converged warp: the counters share a cache line, so
+  // the warp's totals go out through one lane.
+  __device__ void flush_warp(unsigned long long* c) {
+    src = mcd::warp_sum64(src);
+    flights = mcd::warp_sum64(flights);
+    coll = mcd::warp_sum64(coll);
+    absn = mcd::warp_sum64(absn);
+    scat = mcd::warp_sum64(scat);
+    census = mcd::warp_sum64(census);
+    children = mcd::warp_sum64(children);
+    capped = mcd::warp_sum64(capped);
+    dropped = mcd::warp_sum64(dropped);
+    draws = mcd::warp_sum64(draws);
+    exh = mcd::warp_sum64(exh);
+    exd = mcd::warp_sum64(exd);
+    maxd = mcd::warp_max64(maxd);
+    if ((threadIdx.x & 31u) == 0u) flush(c);
+  }
 };
 
 template <int M, bool HASH>
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
     // particle (the same draw, in the same stream order, as drawing it in place)
     if (redraw) mu = mcx::two_u_minus_1(r.next_n(l));
   }
-  lc.flush(a.counts);
+  lc.flush_warp(a.counts);
 }
 
 }  // namespace

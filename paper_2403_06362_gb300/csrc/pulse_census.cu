@@ -109,6 +109,25 @@ struct CensusCounts {
     if (splits) atomicAdd(c + MC_C_SPLITS, (unsigned long long)splits);
     if (kills) atomicAdd(c + MC_C_ROULETTE_KILLS, (unsigned long long)kills);
   }
+  // The same for a whole converged warp: the counters share a cache line, so
+  // the warp's totals go out through one lane.
+  __device__ void flush_warp(unsigned long long* c) {
+    src = mcd::warp_sum64(src);
+    flights = mcd::warp_sum64(flights);
+    coll = mcd::warp_sum64(coll);
+    absn = mcd::warp_sum64(absn);
+    scat = mcd::warp_sum64(scat);
+    census = mcd::warp_sum64(census);
+    children = mcd::warp_sum64(children);
+    capped = mcd::warp_sum64(capped);
+    dropped = mcd::warp_sum64(dropped);
+    draws = mcd::warp_sum64(draws);
+    maxd = mcd::warp_max64(maxd);
+    banked = mcd::warp_sum64(banked);
+    splits = mcd::warp_sum64(splits);
+    kills = mcd::warp_sum64(kills);
+    if ((threadIdx.x & 31u) == 0u) flush(c);
+  }
   __device__ void stream_end(uint64_t d) {
     draws += d;
     if (d > maxd) maxd = d;
@@ -350,7 +369,7 @@ __global__ void __maxnreg__(96) pulse_census_kernel(const CensusArgs a) {
     // one code path draws the direction of a scattered or a popped particle
     if (redraw) mu = mcx::two_u_minus_1(r.next_n(l));
   }
-  lc.flush(a.counts);
+  lc.flush_warp(a.counts);
 }
 
 // Control of each group after a phase: GroupCtl from the exact weight

@@ -171,6 +171,32 @@ struct LaneCounts {
     if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
     clear();
   }
+  // The same for a whole converged warp: sums first, then one lane's atomics.
+  __device__ void flush_warp(unsigned long long* counts) {
+    const int p = mcd::warp_common_prob(prob);
+    if (p == -2) { flush(counts); return; }
+    if (p < 0) return;
+    const unsigned long long so = mcd::warp_sum64(src), fl = mcd::warp_sum64(flights), co = mcd::warp_sum64(coll),
+                             ab = mcd::warp_sum64(absn), sc = mcd::warp_sum64(scat), lo = mcd::warp_sum64(llo),
+                             hi = mcd::warp_sum64(lhi), cp = mcd::warp_sum64(capped), ex = mcd::warp_sum64(exh),
+                             dr = mcd::warp_sum64(draws), ed = mcd::warp_sum64(exd), mx = mcd::warp_max64(maxd);
+    if ((threadIdx.x & 31u) == 0u) {
+      unsigned long long* c = counts + (size_t)p * MC_NCOUNT;
+      if (so) atomicAdd(c + MC_C_SOURCE, so);
+      if (fl) atomicAdd(c + MC_C_FLIGHTS, fl);
+      if (co) atomicAdd(c + MC_C_COLLISIONS, co);
+      if (ab) atomicAdd(c + MC_C_ABSORPTIONS, ab);
+      if (sc) atomicAdd(c + MC_C_SCATTERS, sc);
+      if (lo) atomicAdd(c + MC_C_LEAK_LO, lo);
+      if (hi) atomicAdd(c + MC_C_LEAK_HI, hi);
+      if (dr) atomicAdd(c + MC_C_DRAWS, dr);
+      if (ex) atomicAdd(c + MC_C_EXCEED_HIST, ex);
+      if (ed) atomicAdd(c + MC_C_EXCEED_DRAWS, ed);
+      if (cp) atomicAdd(c + MC_C_CAPPED, cp);
+      if (mx) atomicMax(c + MC_C_MAX_DRAWS, mx);
+    }
+    clear();
+  }
 };
 
 __device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, uint64_t gi) {
@@ -370,7 +396,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
       }
     }
   }
-  lc.flush(a.counts);
+  lc.flush_warp(a.counts);
 
   if constexpr (SMEM) {
     __syncthreads();
