@@ -73,66 +73,6 @@ struct BoxArgs {
   uint64_t event_cap;
 };
 
-struct BoxCounts {
-  int prob;
-  uint32_t src, flights, coll, leaks, kills, splits, children, capped, exh;
-  uint64_t draws, exd, maxd;
-  __device__ void clear() {
-    src = flights = coll = leaks = kills = splits = children = capped = exh = 0u;
-    draws = exd = maxd = 0ull;
-  }
-  __device__ void flush(unsigned long long* counts) {
-    if (prob < 0) return;
-    unsigned long long* c = counts + (size_t)prob * MC_NCOUNT;
-    if (src) atomicAdd(c + MC_C_SOURCE, (unsigned long long)src);
-    if (flights) atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)flights);
-    if (coll) {
-      atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)coll);
-      atomicAdd(c + MC_C_SCATTERS, (unsigned long long)coll);
-    }
-    if (leaks) atomicAdd(c + MC_C_LEAK_HI, (unsigned long long)leaks);
-    if (kills) atomicAdd(c + MC_C_ROULETTE_KILLS, (unsigned long long)kills);
-    if (splits) atomicAdd(c + MC_C_SPLITS, (unsigned long long)splits);
-    if (children) atomicAdd(c + MC_C_CHILDREN, (unsigned long long)children);
-    if (capped) atomicAdd(c + MC_C_CAPPED, (unsigned long long)capped);
-    if (exh) atomicAdd(c + MC_C_EXCEED_HIST, (unsigned long long)exh);
-    if (draws) atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
-    if (exd) atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)exd);
-    if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
-    clear();
-  }
-  // The same for a whole converged warp: sums first, then one lane's atomics
-  // (a problem's counters share a cache line).
-  __device__ void flush_warp(unsigned long long* counts) {
-    const int p = mcd::warp_common_prob(prob);
-    if (p == -2) { flush(counts); return; }
-    if (p < 0) return;
-    const unsigned long long so = mcd::warp_sum64(src), fl = mcd::warp_sum64(flights), co = mcd::warp_sum64(coll),
-                             le = mcd::warp_sum64(leaks), ki = mcd::warp_sum64(kills), sp = mcd::warp_sum64(splits),
-                             ch = mcd::warp_sum64(children), cp = mcd::warp_sum64(capped), ex = mcd::warp_sum64(exh),
-                             dr = mcd::warp_sum64(draws), ed = mcd::warp_sum64(exd), mx = mcd::warp_max64(maxd);
-    if ((threadIdx.x & 31u) == 0u) {
-      unsigned long long* c = counts + (size_t)p * MC_NCOUNT;
-      if (so) atomicAdd(c + MC_C_SOURCE, so);
-      if (fl) atomicAdd(c + MC_C_FLIGHTS, fl);
-      if (co) {
-        atomicAdd(c + MC_C_COLLISIONS, co);
-        atomicAdd(c + MC_C_SCATTERS, co);
-      }
-      if (le) atomicAdd(c + MC_C_LEAK_HI, le);
-      if (ki) atomicAdd(c + MC_C_ROULETTE_KILLS, ki);
-      if (sp) atomicAdd(c + MC_C_SPLITS, sp);
-      if (ch) atomicAdd(c + MC_C_CHILDREN, ch);
-      if (cp) atomicAdd(c + MC_C_CAPPED, cp);
-      if (ex) atomicAdd(c + MC_C_EXCEED_HIST, ex);
-      if (dr) atomicAdd(c + MC_C_DRAWS, dr);
-      if (ed) atomicAdd(c + MC_C_EXCEED_DRAWS, ed);
-      if (mx) atomicMax(c + MC_C_MAX_DRAWS, mx);
-    }
-    clear();
-  }
-};
-
 __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64_t gi) {
   uint32_t lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -173,7 +113,7 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
 
   uint64_t pool_next = 0, pool_end = 0;
   bool more = true, alive = false, primary = false;
-  BoxCounts lc;
+  mcb::BoxCounts lc;
   lc.prob = -1;
   lc.clear();
   const BoxDev* P = probs;

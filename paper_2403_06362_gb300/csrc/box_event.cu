@@ -194,34 +194,33 @@ __global__ void __launch_bounds__(256) refill_kernel(Args a) {
   }
 }
 
-// outcome: mcb::kBoxLeak, kBoxKilled, or -1 (event cap)
-__device__ void finish(const Args& a, uint32_t s, int outcome, uint64_t rng_x, uint64_t draws) {
+// outcome: mcb::kBoxLeak, kBoxKilled, or -1 (event cap).  The particle's
+// counts go to the thread's counters `ec` (flushed by its warp at the end of
+// the kernel, or here when the problem changes).
+__device__ void finish(const Args& a, uint32_t s, int outcome, uint64_t rng_x, uint64_t draws, mcb::BoxCounts& ec) {
   const Bank& b = a.b;
   const uint32_t pi = b.prob[s];
   const BoxDev& P = a.probs[pi];
-  unsigned long long* c = a.counts + (size_t)pi * MC_NCOUNT;
+  if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
   const bool prim = b.primary[s] != 0u;
-  if (prim) atomicAdd(c + MC_C_SOURCE, 1ull);
-  atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)b.events[s]);
-  const uint32_t co = b.coll[s];
-  if (co) {
-    atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)co);
-    atomicAdd(c + MC_C_SCATTERS, (unsigned long long)co);
-  }
-  if (outcome == mcb::kBoxLeak) atomicAdd(c + MC_C_LEAK_HI, 1ull);
-  else if (outcome == mcb::kBoxKilled) atomicAdd(c + MC_C_ROULETTE_KILLS, 1ull);
-  else atomicAdd(c + MC_C_CAPPED, 1ull);
-  atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
-  atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)draws);
+  if (prim) ++ec.src;
+  ec.flights += (uint32_t)b.events[s];
+  ec.coll += b.coll[s];
+  if (outcome == mcb::kBoxLeak) ++ec.leaks;
+  else if (outcome == mcb::kBoxKilled) ++ec.kills;
+  else ++ec.capped;
+  ec.draws += draws;
+  if (draws > ec.maxd) ec.maxd = draws;
   if (prim) {
     if (P.stride_q != 0 && draws > P.stride_q) {
-      atomicAdd(c + MC_C_EXCEED_HIST, 1ull);
-      atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)(draws - P.stride_q));
+      ++ec.exh;
+      ec.exd += draws - P.stride_q;
     }
     const uint64_t gi = b.gi[s];
     if (a.hist_state) a.hist_state[gi] = rng_x & a.lcg.mask;
     if (a.hist_draws) a.hist_draws[gi] = draws;
   }
+  if (ec.draws > (1ull << 31) || ec.flights > (1u << 30)) ec.flush(a.counts);
   const unsigned int k = atomicAdd(&b.ctl->nfree, 1u);
   b.freeq[k] = s;
 }
@@ -235,13 +234,16 @@ __global__ void __launch_bounds__(256) flight_kernel(Args a) {
   uint32_t* fnext = cur ? b.fq0 : b.fq1;
   unsigned int* nnext = &b.ctl->nfq[cur ^ 1u];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  mcb::BoxCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t s = fq[t];
     const BoxDev& P = a.probs[b.prob[s]];
     mcs::Rng<M> r{b.rng[s], b.draws[s]};
     const uint64_t ev = b.events[s];
     if (ev == a.event_cap) {
-      finish(a, s, -1, r.x, r.draws);
+      finish(a, s, -1, r.x, r.draws, ec);
       continue;
     }
     b.events[s] = ev + 1;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256) flight_kernel(Args a) {
     load_part<T>(b, s, q);
     const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, a.tally + b.tbase[s]);
     if (o == mcb::kBoxLeak) {
-      finish(a, s, o, r.x, r.draws);
+      finish(a, s, o, r.x, r.draws, ec);
       continue;
     }
     b.rng[s] = r.x;
@@ -259,6 +261,7 @@ __global__ void __launch_bounds__(256) flight_kernel(Args a) {
     if (o == mcb::kBoxCollide) warp_append(&b.ctl->ncq, b.cq, s);
     else warp_append(nnext, fnext, s);
   }
+  ec.flush_warp(a.counts);
 }
 
 template <int M, typename T>
@@ -269,6 +272,9 @@ __global__ void __launch_bounds__(256) collide_kernel(Args a) {
   uint32_t* fq = nxt ? b.fq1 : b.fq0;
   unsigned int* nfq = &b.ctl->nfq[nxt];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  mcb::BoxCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t s = b.cq[t];
     const uint32_t pi = b.prob[s];
@@ -279,14 +285,14 @@ __global__ void __launch_bounds__(256) collide_kernel(Args a) {
     b.coll[s] += 1u;
     const int o = mcb::box_collide<M, T>(P, r, a.lcg, q);
     if (o == mcb::kBoxKilled) {
-      finish(a, s, o, r.x, r.draws);
+      finish(a, s, o, r.x, r.draws, ec);
       continue;
     }
     if (o >= mcb::kSplitBase + 2) {
       const uint32_t ns = (uint32_t)(o - mcb::kSplitBase);
-      unsigned long long* c = a.counts + (size_t)pi * MC_NCOUNT;
-      atomicAdd(c + MC_C_SPLITS, 1ull);
-      atomicAdd(c + MC_C_CHILDREN, (unsigned long long)(ns - 1));
+      if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
+      ++ec.splits;
+      ec.children += ns - 1;
       for (uint32_t k = 0; k + 1 < ns; ++k) {
         const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
         if (idx < a.child_cap)
@@ -298,6 +304,7 @@ __global__ void __launch_bounds__(256) collide_kernel(Args a) {
     store_part<T>(b, s, q);
     warp_append(nfq, fq, s);
   }
+  ec.flush_warp(a.counts);
 }
 
 __global__ void advance_kernel(Args a) {
@@ -323,6 +330,9 @@ __global__ void __launch_bounds__(256) tail_kernel(Args a) {
   const uint32_t n = b.ctl->nfq[cur];
   const uint32_t* fq = cur ? b.fq1 : b.fq0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  mcb::BoxCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t s = fq[t];
     const uint32_t pi = b.prob[s];
@@ -345,9 +355,9 @@ __global__ void __launch_bounds__(256) tail_kernel(Args a) {
       if (c == mcb::kBoxKilled) { outcome = c; break; }
       if (c >= mcb::kSplitBase + 2) {
         const uint32_t ns = (uint32_t)(c - mcb::kSplitBase);
-        unsigned long long* cn = a.counts + (size_t)pi * MC_NCOUNT;
-        atomicAdd(cn + MC_C_SPLITS, 1ull);
-        atomicAdd(cn + MC_C_CHILDREN, (unsigned long long)(ns - 1));
+        if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
+        ++ec.splits;
+        ec.children += ns - 1;
         for (uint32_t k = 0; k + 1 < ns; ++k) {
           const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
           if (idx < a.child_cap)
@@ -357,8 +367,9 @@ __global__ void __launch_bounds__(256) tail_kernel(Args a) {
     }
     b.events[s] = ev;
     b.coll[s] = co;
-    finish(a, s, outcome, r.x, r.draws);
+    finish(a, s, outcome, r.x, r.draws, ec);
   }
+  ec.flush_warp(a.counts);
 }
 
 constexpr int kIter = 32;

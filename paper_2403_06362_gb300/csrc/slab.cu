@@ -145,60 +145,6 @@ __device__ __forceinline__ uint32_t pool_get(const unsigned long long* e, mcs::R
   return (uint32_t)(e[6] >> 32);
 }
 
-// Per-lane counters for the lane's current problem.
-struct LaneCounts {
-  int prob;
-  uint32_t src, flights, coll, absn, scat, llo, lhi, capped, exh;
-  uint64_t draws, exd, maxd;
-  __device__ void clear() {
-    src = flights = coll = absn = scat = llo = lhi = capped = exh = 0u;
-    draws = exd = maxd = 0ull;
-  }
-  __device__ void flush(unsigned long long* counts) {
-    if (prob < 0) return;
-    unsigned long long* c = counts + (size_t)prob * MC_NCOUNT;
-    if (src) atomicAdd(c + MC_C_SOURCE, (unsigned long long)src);
-    if (flights) atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)flights);
-    if (coll) atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)coll);
-    if (absn) atomicAdd(c + MC_C_ABSORPTIONS, (unsigned long long)absn);
-    if (scat) atomicAdd(c + MC_C_SCATTERS, (unsigned long long)scat);
-    if (llo) atomicAdd(c + MC_C_LEAK_LO, (unsigned long long)llo);
-    if (lhi) atomicAdd(c + MC_C_LEAK_HI, (unsigned long long)lhi);
-    if (draws) atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
-    if (exh) atomicAdd(c + MC_C_EXCEED_HIST, (unsigned long long)exh);
-    if (exd) atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)exd);
-    if (capped) atomicAdd(c + MC_C_CAPPED, (unsigned long long)capped);
-    if (maxd) atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)maxd);
-    clear();
-  }
-  // The same for a whole converged warp: sums first, then one lane's atomics.
-  __device__ void flush_warp(unsigned long long* counts) {
-    const int p = mcd::warp_common_prob(prob);
-    if (p == -2) { flush(counts); return; }
-    if (p < 0) return;
-    const unsigned long long so = mcd::warp_sum64(src), fl = mcd::warp_sum64(flights), co = mcd::warp_sum64(coll),
-                             ab = mcd::warp_sum64(absn), sc = mcd::warp_sum64(scat), lo = mcd::warp_sum64(llo),
-                             hi = mcd::warp_sum64(lhi), cp = mcd::warp_sum64(capped), ex = mcd::warp_sum64(exh),
-                             dr = mcd::warp_sum64(draws), ed = mcd::warp_sum64(exd), mx = mcd::warp_max64(maxd);
-    if ((threadIdx.x & 31u) == 0u) {
-      unsigned long long* c = counts + (size_t)p * MC_NCOUNT;
-      if (so) atomicAdd(c + MC_C_SOURCE, so);
-      if (fl) atomicAdd(c + MC_C_FLIGHTS, fl);
-      if (co) atomicAdd(c + MC_C_COLLISIONS, co);
-      if (ab) atomicAdd(c + MC_C_ABSORPTIONS, ab);
-      if (sc) atomicAdd(c + MC_C_SCATTERS, sc);
-      if (lo) atomicAdd(c + MC_C_LEAK_LO, lo);
-      if (hi) atomicAdd(c + MC_C_LEAK_HI, hi);
-      if (dr) atomicAdd(c + MC_C_DRAWS, dr);
-      if (ex) atomicAdd(c + MC_C_EXCEED_HIST, ex);
-      if (ed) atomicAdd(c + MC_C_EXCEED_DRAWS, ed);
-      if (cp) atomicAdd(c + MC_C_CAPPED, cp);
-      if (mx) atomicMax(c + MC_C_MAX_DRAWS, mx);
-    }
-    clear();
-  }
-};
-
 __device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, uint64_t gi) {
   uint32_t lo = 0, hi = n - 1;  // largest i with hist_begin <= gi
   while (lo < hi) {
@@ -249,7 +195,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   uint64_t pool_next = 0, pool_end = 0;
   bool more = true;
   bool alive = false;
-  LaneCounts lc;
+  mcs::LaneCounts lc;
   lc.prob = -1;
   lc.clear();
 

@@ -204,30 +204,33 @@ __global__ void __launch_bounds__(256) ev_refill_kernel(EvArgs a) {
   }
 }
 
-// Ends the history in `slot`: counters, per-history outputs, free the slot.
-__device__ void ev_finish(const EvArgs& a, uint32_t slot, int outcome, uint64_t rng_x, uint64_t draws) {
+// Ends the history in `slot`: counters (into the thread's `ec`, flushed by
+// its warp at the end of the kernel or here when the problem changes),
+// per-history outputs, free the slot.
+__device__ void ev_finish(const EvArgs& a, uint32_t slot, int outcome, uint64_t rng_x, uint64_t draws,
+                          mcs::LaneCounts& ec) {
   const EvBank& b = a.b;
   const uint32_t pi = b.prob[slot];
   const SlabDev& P = a.probs[pi];
-  unsigned long long* c = a.counts + (size_t)pi * MC_NCOUNT;
-  atomicAdd(c + MC_C_SOURCE, 1ull);
-  atomicAdd(c + MC_C_FLIGHTS, (unsigned long long)b.events[slot]);
-  const uint64_t co = b.coll[slot], sc = b.scat[slot];
-  if (co) atomicAdd(c + MC_C_COLLISIONS, (unsigned long long)co);
-  if (sc) atomicAdd(c + MC_C_SCATTERS, (unsigned long long)sc);
-  if (outcome == mcs::kAbsorbed) atomicAdd(c + MC_C_ABSORPTIONS, 1ull);
-  else if (outcome == mcs::kLeakLo) atomicAdd(c + MC_C_LEAK_LO, 1ull);
-  else if (outcome == mcs::kLeakHi) atomicAdd(c + MC_C_LEAK_HI, 1ull);
-  else atomicAdd(c + MC_C_CAPPED, 1ull);
-  atomicAdd(c + MC_C_DRAWS, (unsigned long long)draws);
-  atomicMax(c + MC_C_MAX_DRAWS, (unsigned long long)draws);
+  if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
+  ++ec.src;
+  ec.flights += (uint32_t)b.events[slot];
+  ec.coll += (uint32_t)b.coll[slot];
+  ec.scat += (uint32_t)b.scat[slot];
+  if (outcome == mcs::kAbsorbed) ++ec.absn;
+  else if (outcome == mcs::kLeakLo) ++ec.llo;
+  else if (outcome == mcs::kLeakHi) ++ec.lhi;
+  else ++ec.capped;
+  ec.draws += draws;
+  if (draws > ec.maxd) ec.maxd = draws;
   if (P.stride_q != 0 && draws > P.stride_q) {
-    atomicAdd(c + MC_C_EXCEED_HIST, 1ull);
-    atomicAdd(c + MC_C_EXCEED_DRAWS, (unsigned long long)(draws - P.stride_q));
+    ++ec.exh;
+    ec.exd += draws - P.stride_q;
   }
   const uint64_t gi = b.gi[slot];
   if (a.hist_state) a.hist_state[gi] = rng_x & a.lcg.mask;
   if (a.hist_draws) a.hist_draws[gi] = draws;
+  if (ec.draws > (1ull << 31) || ec.flights > (1u << 30)) ec.flush(a.counts);
   const unsigned int k = atomicAdd(&b.ctl->nfree, 1u);
   b.freeq[k] = slot;
 }
@@ -240,13 +243,16 @@ __global__ void __launch_bounds__(256) ev_flight_kernel(EvArgs a) {
   const uint32_t* fq = cur ? b.fq1 : b.fq0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  mcs::LaneCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t slot = fq[t];
     const SlabDev& P = a.probs[b.prob[slot]];
     mcs::Rng<M> r{b.rng[slot], b.draws[slot]};
     const uint64_t ev = b.events[slot];
     if (ev == a.event_cap) {
-      ev_finish(a, slot, -1, r.x, r.draws);
+      ev_finish(a, slot, -1, r.x, r.draws, ec);
       continue;
     }
     b.events[slot] = ev + 1;
@@ -259,7 +265,7 @@ __global__ void __launch_bounds__(256) ev_flight_kernel(EvArgs a) {
     const mcs::Sink sink{a.tally + b.tbase[slot], nullptr, nullptr};
     const int o = mcs::slab_flight<M, F32>(P, r, a.lcg, q, sink);
     if (o != mcs::kCollide) {
-      ev_finish(a, slot, o, r.x, r.draws);
+      ev_finish(a, slot, o, r.x, r.draws, ec);
       continue;
     }
     b.rng[slot] = r.x;
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(256) ev_flight_kernel(EvArgs a) {
     if constexpr (F32) b.xf[slot] = q.xf; else b.x[slot] = q.x;
     warp_append(&b.ctl->ncq, b.cq, slot);
   }
+  ec.flush_warp(a.counts);
 }
 
 template <int M, bool F32>
@@ -278,6 +285,9 @@ __global__ void __launch_bounds__(256) ev_collide_kernel(EvArgs a) {
   unsigned int* nfq = &b.ctl->nfq[nxt];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  mcs::LaneCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t slot = b.cq[t];
     const SlabDev& P = a.probs[b.prob[slot]];
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(256) ev_collide_kernel(EvArgs a) {
     b.coll[slot] += 1;
     const int o = mcs::slab_collide<M, F32>(P, r, a.lcg, q);
     if (o == mcs::kAbsorbed) {
-      ev_finish(a, slot, o, r.x, r.draws);
+      ev_finish(a, slot, o, r.x, r.draws, ec);
       continue;
     }
     b.scat[slot] += 1;
@@ -304,6 +314,7 @@ __global__ void __launch_bounds__(256) ev_collide_kernel(EvArgs a) {
     }
     warp_append(nfq, fq, slot);
   }
+  ec.flush_warp(a.counts);
 }
 
 __global__ void ev_advance_kernel(EvArgs a) {
@@ -328,6 +339,9 @@ __global__ void __launch_bounds__(256) ev_tail_kernel(EvArgs a) {
   const uint32_t* fq = cur ? b.fq1 : b.fq0;
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  mcs::LaneCounts ec;
+  ec.prob = -1;
+  ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
     const uint32_t slot = fq[t];
     const SlabDev& P = a.probs[b.prob[slot]];
@@ -351,8 +365,9 @@ __global__ void __launch_bounds__(256) ev_tail_kernel(EvArgs a) {
     b.events[slot] = ev;
     b.coll[slot] += co;
     b.scat[slot] += sc;
-    ev_finish(a, slot, outcome, r.x, r.draws);
+    ev_finish(a, slot, outcome, r.x, r.draws, ec);
   }
+  ec.flush_warp(a.counts);
 }
 
 constexpr int kIterPerBatch = 32;
