@@ -112,6 +112,20 @@ def test_large_blocks_with_staged_tally_and_pool(env, precision):
         assert np.array_equal(counts_of(t, 1), counts_of(base, 1))
 
 
+def test_staged_tally_near_the_shared_memory_limit(env, oracle):
+    """A 25 600-slot tally forced into shared memory (200 KiB): with the edge
+    tables and the compaction pool it would not fit, so the launch gives them
+    up; the bits equal the global-atomic run's and the oracle's."""
+    probs = [W.slab_problem(50.0, 1.0, 0.9, 4000, 2560, 10, W.SEED_HASH)]
+    staged, _ = gpu_run(env, probs, tally_mode=1)
+    direct, _ = gpu_run(env, probs, n_hist_out=False, tally_mode=2)
+    assert np.array_equal(staged.bins.cpu().numpy(), direct.bins.cpu().numpy())
+    assert np.array_equal(counts_of(staged, 1), counts_of(direct, 1))
+    o = oracle_run(oracle, probs)
+    assert np.array_equal(staged.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert_tally_close(staged.bins.cpu().numpy(), o["tally"])
+
+
 def test_ranges_accumulate_to_the_same_bits(env):
     mc, ctx, torch = env
     probs = W.slab_small(W.SEED_STRIDE, n_histories=20_000)
