@@ -656,8 +656,21 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
   cudaEvent_t e0, e1;
   MC_TRY_CUDA(cudaEventCreate(&e0));
   MC_TRY_CUDA(cudaEventCreate(&e1));
+  // a warm-up run, then one timed run of r
+  auto time_run = [&](mc_run_config& r, float* ms) {
+    int rs = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);
+    if (rs == MC_OK) rs = mci::cuda_status(cudaEventRecord(e0, s), "cudaEventRecord");
+    if (rs == MC_OK) rs = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);
+    if (rs == MC_OK) rs = mci::cuda_status(cudaEventRecord(e1, s), "cudaEventRecord");
+    if (rs == MC_OK) rs = mci::cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    if (rs == MC_OK) cudaEventElapsedTime(ms, e0, e1);
+    return rs;
+  };
   float best_t = 0.0f;
   bool have = false;
+  mc_run_config best_hist{}, event{};
+  float best_hist_t = 0.0f;
+  bool have_hist = false, have_event = false;
   for (const Cand& c : cands) {
     mc_run_config r = *base;
     r.schedule = c.schedule;
@@ -667,18 +680,38 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
     r.accumulate = 0;
     r.range_begin = start;
     r.range_end = start + S;
-    st = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);  // warm-up
-    if (st == MC_OK) st = mci::cuda_status(cudaEventRecord(e0, s), "cudaEventRecord");
-    if (st == MC_OK) st = transport_run_impl(ctx, lcg, problems, n_problems, &r, &t2, total, s);
-    if (st == MC_OK) st = mci::cuda_status(cudaEventRecord(e1, s), "cudaEventRecord");
-    if (st == MC_OK) st = mci::cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
-    if (st != MC_OK) break;
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    st = time_run(r, &ms);
+    if (st != MC_OK) break;
     if (!have || ms < best_t) {
       best_t = ms;
       *best = r;
       have = true;
+    }
+    if (c.schedule == MC_SCHED_HISTORY && (!have_hist || ms < best_hist_t)) {
+      best_hist_t = ms;
+      best_hist = r;
+      have_hist = true;
+    }
+    if (c.schedule == MC_SCHED_EVENT) {
+      event = r;
+      have_event = true;
+    }
+  }
+  // The sample ranks the shapes of one schedule, but the two schedules scale
+  // differently from a sample to the whole (the history schedule's tail is a
+  // larger share of a small run): when the event schedule wins the sample,
+  // the best history shape and it are timed again on the whole range.
+  if (st == MC_OK && have_hist && have_event && S < total && best->schedule == MC_SCHED_EVENT) {
+    mc_run_config rh = best_hist, re = event;
+    rh.range_begin = re.range_begin = 0;
+    rh.range_end = re.range_end = total;
+    float th = 0.0f, te = 0.0f;
+    st = time_run(rh, &th);
+    if (st == MC_OK) st = time_run(re, &te);
+    if (st == MC_OK) {
+      *best = th <= te ? best_hist : event;
+      best_t = th <= te ? th : te;
     }
   }
   cudaEventDestroy(e0);
