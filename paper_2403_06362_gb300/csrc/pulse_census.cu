@@ -238,8 +238,10 @@ __global__ void __maxnreg__(96) pulse_census_kernel(const CensusArgs a) {
           const BankRec e = staged ? si->e : a.in[item];
           grp = e.group;
           const GroupCtl gc = staged ? si->gc : a.ctl[grp - a.group_begin];
-          const double xi = (double)(mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11) * 0x1p-53;
-          const uint64_t n = (uint64_t)floor(e.w * gc.ratio + xi);
+          // xi = h 2^-53 and the floor (of a non-negative sum) on the integer pipes
+          const uint64_t h = mcd::hash64(kOneOffKey + (a.phase - 1), e.s) >> 11;
+          const double xi = mcd::u53_to_double((uint32_t)(h >> 32), (uint32_t)h);
+          const uint64_t n = mcx::floor_nonneg(e.w * gc.ratio + xi);
           if (n == 0) {
             ++lc.kills;
             lc.stream_end(e.draws);
