@@ -3,7 +3,7 @@ the host through the C ABI, against ln(1 - u) computed to 40 significant
 digits with Python's decimal module and rounded once.  Every uniform of the
 library is a multiple of 2^-53 in [0, 1), so those are the inputs: uniform,
 log-uniform over every binade down to 2^-53, and the edges of the two
-branches and of the 128 table cells."""
+branches and of the 1024 table cells."""
 import math
 import random
 from decimal import Decimal, getcontext
@@ -37,9 +37,9 @@ def inputs():
     for e in range(1, 54):  # every binade [2^-e, 2^-e+1)
         us += [(2**(53 - e) + rng.getrandbits(53 - e)) * 2.0**-53 for _ in range(40)]
     us += [2.0**-53, 2.0**-8 - 2.0**-53, 2.0**-8, 2.0**-8 + 2.0**-53, 0.5, 1.0 - 2.0**-53, 1.0 - 2.0**-52]
-    for j in range(129):  # x = 1 - u on the edges of the table cells, in a few binades
+    for j in range(1025):  # x = 1 - u on the edges of the 1024 table cells, in a few binades
         for k in (1, 4, 30):
-            x = (1.0 + j / 128.0) * 2.0**-k
+            x = (1.0 + j / 1024.0) * 2.0**-k
             if 0.0 < x < 1.0:
                 us += [1.0 - x, 1.0 - x - 2.0**-53, 1.0 - x + 2.0**-53]
     return [u for u in us if 0.0 < u < 1.0]
@@ -56,6 +56,14 @@ def test_within_one_ulp_of_correctly_rounded(mc):
         worst = max(worst, err)
         assert err < 1.0, (u.hex(), err)
     assert worst > 0.5  # the test does measure something
+
+
+def test_table_branch_within_a_hair_of_correct_rounding(mc):
+    # u >= 2^-8: the fixed-point sum is accurate to about 2^-68 against a
+    # result of at least 2^-8 (an ulp of at least 2^-60), so the rounding can
+    # miss only by a small fraction of an ulp past the halfway point
+    worst = max(ulp_error(mc.mc_log1m(u), u) for u in inputs() if u >= 2.0**-8)
+    assert worst < 0.5005, worst
 
 
 def test_mostly_correctly_rounded(mc):
