@@ -38,6 +38,11 @@ def recip_inputs():
     for n in range(1, 3000):  # mantissas near 1 and near 2
         ys.append(from_bits((1023 << 52) | n))
         ys.append(from_bits((1023 << 52) | ((1 << 52) - n)))
+    for j in range(1024):  # mantissas on and next to the edges of the 1024 cells of [1, 2)
+        for d in (0, 1, 2, (1 << 42) - 1, (1 << 42) - 2):
+            m = (j << 42) + d
+            if 0 < m < (1 << 52):
+                ys.append(from_bits((1022 << 52) | m))
     ys += [2.0**k for k in range(-1020, 1021, 7)]
     ys += [(2 * n - 2**53) * 2.0**-53 for n in range(1, 4000) if n != 2**52]  # slab directions
     ys += [-y for y in ys[:50000]]
