@@ -37,18 +37,19 @@ METRIC = ("particle histories/sec and RNG draws/sec on 1 GB300 "
           "(hash vs stride, % int-pipe roofline)")
 N_STREAMS = 2**26
 DRAWS = 64
-# Integer operations per draw of the formulation in csrc/mc_device.cuh
-# (u01_m63_bits_fast): 64-bit multiply-add as IMAD.WIDE + 2 IMAD with the
-# increment folded in (3); extraction of the top 53 of the 63 state bits:
-# funnel shift, shift, shift (3); exact integer-to-fp64 assembly: clz,
-# funnel shift, shift, exponent multiply-add, add (5); range flag for the
-# exact redo (1); 64-bit digest add (2).
-OPS_PER_DRAW = 14
+# Operations per draw of the formulation in csrc/rng.cu (draw_digest_m63_kernel,
+# on the doubled state z = 2x): 64-bit multiply-add as IMAD.WIDE + 2 IMAD with
+# the increment folded in (3); normalising shift, one bfind (1); the 53 uniform
+# bits shifted into place as two words: funnel shift, shift, funnel shift,
+# shift (4); the shift summed for the exponent field (1, fp32 pipe); digest add,
+# one three-operand 64-bit add per two draws (1).  The exponent field and the
+# range check are folded into those sums.
+OPS_PER_DRAW = 10
 E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 # DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
 # the ncu capture summarised in profiles/draw_digest_m63_kernel_rng_microbench.md
 # (mean of the hash and stride launches).  Set to None when the kernel changes.
-DRAW_KERNEL_TRAFFIC_BYTES = 1.0127e9
+DRAW_KERNEL_TRAFFIC_BYTES = 1.0128e9
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 

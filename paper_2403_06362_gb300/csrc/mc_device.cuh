@@ -111,22 +111,48 @@ __device__ __forceinline__ double u01_m63(uint64_t x) {
   return u53_to_double(hi, lo);
 }
 
-// Branch-free form of u01_m63's bit pattern for the digest kernels: exact
-// whenever the top 21 of the 53 output bits are not all zero.  s_out > 20
-// flags the other case (probability 2^-21 per draw); the caller then redoes
-// the stream with u01_m63.  With t = (high word << 1), clz(t) is directly
-// the normalising shift s = clz(n) - 11 of the 53-bit integer n.
-__device__ __forceinline__ uint64_t u01_m63_bits_fast(uint64_t x, uint32_t& s_out) {
-  const uint32_t xlo = (uint32_t)x, xhi = (uint32_t)(x >> 32);
-  const uint32_t lo = __funnelshift_r(xlo, xhi, 10);
-  const uint32_t t = xhi << 1;
-  const uint32_t s = __clz(t);
-  const uint32_t hi = t >> 11;
-  const uint32_t rhi = __funnelshift_l(lo, hi, s) + ((1021u - s) << 20);
-  const uint32_t rlo = __funnelshift_l(0u, lo, s);
-  s_out = s;
-  return ((uint64_t)rhi << 32) | rlo;
+// Pieces of the digest kernels' branch-free draw for m = 63.  They run on
+// the doubled state z = 2x (mod 2^64), which follows z' = g z + 2c and
+// holds the uniform's 53 bits n = z >> 11 at the top of the word.  With s
+// the normalising shift of n (s = clz(z_hi) when z_hi != 0), the fp64 bit
+// pattern of u = n 2^-53 is (1021 - s) 2^52 + (n << s): n << s has its
+// leading 1 at bit 52, which carries one into the exponent field.
+
+// clz(v) for v != 0; all ones for v = 0 (PTX bfind.shiftamt).
+__device__ __forceinline__ uint32_t clz_or_ones(uint32_t v) {
+  uint32_t r;
+  asm("bfind.shiftamt.u32 %0, %1;" : "=r"(r) : "r"(v));
+  return r;
 }
+
+// v << s with the shift clamped (PTX shl: 0 for s >= 32).
+__device__ __forceinline__ uint32_t shl_clamped(uint32_t v, uint32_t s) {
+  uint32_t r;
+  asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(v), "r"(s));
+  return r;
+}
+
+// n << s for s = clz_or_ones(z_hi) < 32 (exact then: n < 2^(53 - s)); any
+// value for s = all ones.
+__device__ __forceinline__ uint64_t n_shifted_m63(uint64_t z, uint32_t s) {
+  const uint32_t zl = (uint32_t)z, zh = (uint32_t)(z >> 32);
+  const uint32_t nl = __funnelshift_r(zl, zh, 11), nh = zh >> 11;
+  return ((uint64_t)__funnelshift_l(nl, nh, s) << 32) | shl_clamped(nl, s);
+}
+
+// Adds s to a sum kept as the bit pattern of an fp32 subnormal (value
+// s 2^-149), on the fp32 pipe.  The sum is exact while it stays below 2^24
+// units; the all-ones s of a z_hi = 0 draw is a NaN pattern and turns the
+// sum into a NaN, which marks the stream.  Explicit PTX, so that no
+// flush-to-zero setting can apply.
+__device__ __forceinline__ float add_count(float acc, uint32_t s) {
+  float r;
+  asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(acc), "f"(__uint_as_float(s)));
+  return r;
+}
+
+// True if a sum kept by add_count met a z_hi = 0 draw (its pattern is a NaN).
+__device__ __forceinline__ bool count_marked(float acc) { return __float_as_uint(acc) > 0x7f800000u; }
 
 // Uniform for any 1 <= m <= 64.
 __device__ __forceinline__ double u01_any(uint64_t x, uint32_t m) {

@@ -11,7 +11,7 @@
 // Draws (Eq. 1) are bound by integer issue: the 64-bit state stays in
 // registers for all draws of a stream, each step is one 64-bit
 // multiply-add (IMAD.WIDE + 2 IMAD), and each uniform is assembled with
-// integer instructions.
+// integer instructions (the digest kernel also counts on the fp32 pipe).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -199,12 +199,21 @@ __global__ void __launch_bounds__(kDrawBlock) draw_kernel(const DrawArgs a) {
 
 // Digest-only draws for m = 63, the integer-issue-bound hot loop.  Each
 // thread carries two streams (i and i + T, T = threads in the grid) for
-// instruction-level parallelism; every uniform is built with the branch-free
-// u01_m63_bits_fast, and the rare stream that met a draw outside its range
-// is recomputed with the exact per-draw path.  DRAWS > 0 fixes the draw
-// count at compile time (fully unrolled); DRAWS = 0 reads it at run time.
+// instruction-level parallelism.  A stream runs on the doubled state
+// z = 2x (mod 2^64), the same recurrence with increment 2c, so that the 53
+// uniform bits sit at the top of the word.  Per draw: the LCG step
+// (IMAD.WIDE + 2 IMAD), the normalising shift s (one bfind), n << s as two
+// words (four shifts), s summed on the otherwise idle fp32 pipe; two draws
+// share one 64-bit add.  The digest is the sum of the draws' fp64 bit
+// patterns, sum(n << s) + (1021 D - sum s) 2^52 (mod 2^64), and equals the
+// per-draw sum of dbits(u01_m63(x)).  A stream whose count sum came out NaN
+// met a draw with z_hi = 0 (probability 2^-32 per draw) and is redone with
+// the exact per-draw path.  DRAWS > 0 fixes the draw count at compile time
+// (fully unrolled); DRAWS = 0 reads it at run time and folds the fp32 count
+// into an integer every 16 draws, so that it stays exact.
 template <int SEED, int DRAWS>
 __global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawArgs a) {
+  static_assert(DRAWS % 2 == 0 && DRAWS * 31 < (1 << 24), "count sum must stay exact");
   __shared__ Affine tab[64];
   if constexpr (SEED == kStride) build_pow2_table(tab, a.g, a.c);
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -214,82 +223,105 @@ __global__ void __launch_bounds__(kDrawBlock) draw_digest_m63_kernel(const DrawA
   uint64_t xs = 0, seed_hash = 0;
   if constexpr (SEED == kHash) seed_hash = mcd::seed_hash_of(a.hier ? mcd::hash64(a.key, a.seed) : a.seed);
   if constexpr (SEED == kStride) xs = skip_by_table(tab, a.x0, a.q * (a.id_begin + tid));
-  const uint64_t g = a.g, c = a.c;
+  const uint64_t g = a.g, c2 = 2ull * a.c;
   for (uint64_t i = tid; i < a.n; i += 2 * nthreads) {
     const uint64_t i2 = i + nthreads;
     const bool two = i2 < a.n;
-    uint64_t x0a, x0b;
-    if constexpr (SEED == kLoad) {
-      x0a = a.states[i];
-      x0b = a.states[two ? i2 : i];
-    } else if constexpr (SEED == kHash) {
-      x0a = mcd::hash_with(a.id_begin + i, seed_hash) & a.mask;
-      x0b = mcd::hash_with(a.id_begin + (two ? i2 : i), seed_hash) & a.mask;
-    } else {
-      x0a = xs & a.mask;
-      x0b = mcd::apply(a.half, xs) & a.mask;
-      xs = mcd::apply(a.sweep, xs);
-    }
-    uint64_t xa = x0a, xb = x0b, da = 0, db = 0;
-    uint32_t sa = 0, sb = 0;
-    uint32_t j = 0;
+    // Starting state (masked) of stream q; called again by the redo.
+    auto start = [&](int q) -> uint64_t {
+      const uint64_t iq = q == 0 ? i : (two ? i2 : i);
+      if constexpr (SEED == kLoad) {
+        return a.states[iq];
+      } else if constexpr (SEED == kHash) {
+        return mcd::hash_with(a.id_begin + iq, seed_hash) & a.mask;
+      } else {
+        return (q == 0 ? xs : mcd::apply(a.half, xs)) & a.mask;
+      }
+    };
+    uint64_t z[2] = {start(0) << 1, start(1) << 1};
+    uint64_t acc[2] = {0ull, 0ull};
+    float cnt[2] = {0.f, 0.f};
+    uint32_t sum_s[2] = {0u, 0u}, marked = 0u;
+    auto fold = [&](int q) {  // run-time count: fp32 partial into the integer sum
+      const uint32_t p = __float_as_uint(cnt[q]);
+      marked |= mcd::count_marked(cnt[q]) ? (1u << q) : 0u;
+      sum_s[q] += p;
+      cnt[q] = 0.f;
+    };
     if constexpr (DRAWS > 0) {
 #pragma unroll
-      for (int t = 0; t < DRAWS; ++t) {
-        uint32_t s1, s2;
-        xa = mcd::lcg_step(xa, g, c);
-        xb = mcd::lcg_step(xb, g, c);
-        da += mcd::u01_m63_bits_fast(xa, s1);
-        db += mcd::u01_m63_bits_fast(xb, s2);
-        sa = max(sa, s1);
-        sb = max(sb, s2);
+      for (int t = 0; t < DRAWS; t += 2) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint64_t y[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            z[q] = g * z[q] + c2;
+            const uint32_t s = mcd::clz_or_ones((uint32_t)(z[q] >> 32));
+            cnt[q] = mcd::add_count(cnt[q], s);
+            y[h] = mcd::n_shifted_m63(z[q], s);
+          }
+          acc[q] += y[0] + y[1];
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) fold(q);
     } else {
+      uint32_t j = 0;
 #pragma unroll 1
       for (; j + 16 <= draws; j += 16) {
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          uint32_t s1, s2;
-          xa = mcd::lcg_step(xa, g, c);
-          xb = mcd::lcg_step(xb, g, c);
-          da += mcd::u01_m63_bits_fast(xa, s1);
-          db += mcd::u01_m63_bits_fast(xb, s2);
-          sa = max(sa, s1);
-          sb = max(sb, s2);
+        for (int t = 0; t < 16; t += 2) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            uint64_t y[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              z[q] = g * z[q] + c2;
+              const uint32_t s = mcd::clz_or_ones((uint32_t)(z[q] >> 32));
+              cnt[q] = mcd::add_count(cnt[q], s);
+              y[h] = mcd::n_shifted_m63(z[q], s);
+            }
+            acc[q] += y[0] + y[1];
+          }
         }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) fold(q);
       }
       for (; j < draws; ++j) {
-        uint32_t s1, s2;
-        xa = mcd::lcg_step(xa, g, c);
-        xb = mcd::lcg_step(xb, g, c);
-        da += mcd::u01_m63_bits_fast(xa, s1);
-        db += mcd::u01_m63_bits_fast(xb, s2);
-        sa = max(sa, s1);
-        sb = max(sb, s2);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          z[q] = g * z[q] + c2;
+          const uint32_t s = mcd::clz_or_ones((uint32_t)(z[q] >> 32));
+          cnt[q] = mcd::add_count(cnt[q], s);
+          acc[q] += mcd::n_shifted_m63(z[q], s);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) fold(q);
+    }
+    uint64_t x[2], d[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      x[q] = z[q] >> 1;  // the final state mod 2^63
+      d[q] = acc[q] + ((uint64_t)((1021u * draws - sum_s[q]) & 0xfffu) << 52);
+      if (marked & (1u << q)) {  // exact redo of stream q
+        uint64_t xr = start(q), dr = 0;
+        for (uint32_t k = 0; k < draws; ++k) {
+          xr = mcd::lcg_step(xr, g, a.c);
+          dr += mcd::dbits(mcd::u01_m63(xr));
+        }
+        x[q] = xr & a.mask;
+        d[q] = dr;
       }
     }
-    if (sa > 20u) {  // exact redo of stream a
-      xa = x0a;
-      da = 0;
-      for (uint32_t k = 0; k < draws; ++k) {
-        xa = mcd::lcg_step(xa, g, c);
-        da += mcd::dbits(mcd::u01_m63(xa));
-      }
-    }
-    if (sb > 20u) {
-      xb = x0b;
-      db = 0;
-      for (uint32_t k = 0; k < draws; ++k) {
-        xb = mcd::lcg_step(xb, g, c);
-        db += mcd::dbits(mcd::u01_m63(xb));
-      }
-    }
-    if (a.states) a.states[i] = xa & a.mask;
-    if (a.digest) a.digest[i] = da;
+    if (a.states) a.states[i] = x[0];
+    if (a.digest) a.digest[i] = d[0];
     if (two) {
-      if (a.states) a.states[i2] = xb & a.mask;
-      if (a.digest) a.digest[i2] = db;
+      if (a.states) a.states[i2] = x[1];
+      if (a.digest) a.digest[i2] = d[1];
     }
+    if constexpr (SEED == kStride) xs = mcd::apply(a.sweep, xs);
   }
 }
 

@@ -186,11 +186,14 @@ def test_digest_only_kernel(env, oracle, draws, n):
     assert np.array_equal(u64(dg), o_dg)
 
 
-@pytest.mark.parametrize("draws", [5, 64])
+@pytest.mark.parametrize("draws", [5, 64, 65])
 def test_digest_kernel_rare_conversion_path(env, oracle, draws):
-    # first states whose top 21 output bits are zero force the exact redo
+    # first states below 2^31 (high word of the doubled state zero) force the
+    # exact redo; those from 2^31 up take the branch-free path with
+    # normalising shifts up to 31
     mc, ctx, torch = env
-    special = np.array([0, 1, 1023, 1024, 2**32, 2**42 - 1, 2**42, 2**43 + 5, 2**52, 2**62], dtype=np.uint64)
+    special = np.array([0, 1, 1023, 1024, 2**31 - 1, 2**31, 2**31 + 1, 2**32 - 1, 2**32, 2**33 - 1,
+                        2**42 - 1, 2**42, 2**43 + 5, 2**52, 2**62, 2**63 - 1], dtype=np.uint64)
     ginv = pow(G, -1, 2**63)
     pre = np.array([((int(x) - CC) * ginv) % 2**63 for x in special], dtype=np.uint64)
     pre = np.concatenate([pre, oracle.seed_hash(M, 1, 0, 101)])
@@ -198,5 +201,19 @@ def test_digest_kernel_rare_conversion_path(env, oracle, draws):
     dg = torch.empty(pre.size, dtype=torch.int64, device="cuda")
     mc.mc_lcg_draw(ctx, mc.make_lcg(), None, 0, v, pre.size, draws, None, dg)
     o_st, _, o_dg = oracle.lcg_draw(M, G, CC, pre, draws, want_u=False)
+    assert np.array_equal(u64(v), o_st)
+    assert np.array_equal(u64(dg), o_dg)
+
+
+def test_digest_kernel_long_streams(env, oracle):
+    # run-time draw count far beyond what one fp32 count sum holds exactly
+    # (the kernel folds it into an integer every 16 draws)
+    mc, ctx, torch = env
+    n, draws = 5, 600_001
+    seeds = oracle.seed_hash(M, 3, 0, n)
+    v = torch.from_numpy(seeds.view(np.int64).copy()).cuda()
+    dg = torch.empty(n, dtype=torch.int64, device="cuda")
+    mc.mc_lcg_draw(ctx, mc.make_lcg(), None, 0, v, n, draws, None, dg)
+    o_st, _, o_dg = oracle.lcg_draw(M, G, CC, seeds, draws, want_u=False)
     assert np.array_equal(u64(v), o_st)
     assert np.array_equal(u64(dg), o_dg)
