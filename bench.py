@@ -47,9 +47,10 @@ DRAWS = 64
 OPS_PER_DRAW = 10
 E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 # DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
-# the ncu capture summarised in profiles/draw_digest_m63_kernel_rng_microbench.md
-# (mean of the hash and stride launches).  Set to None when the kernel changes.
-DRAW_KERNEL_TRAFFIC_BYTES = 1.0128e9
+# an ncu capture of the kernel as it is built (mean of the hash and stride
+# launches).  None: the launch bounds changed after the last capture, which
+# profiles/draw_digest_m63_kernel_rng_microbench.md summarises.
+DRAW_KERNEL_TRAFFIC_BYTES = None
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 
