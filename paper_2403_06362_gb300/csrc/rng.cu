@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kDrawBlock) draw_kernel(const DrawArgs a) {
     double* up = WANT_U ? a.u + i : nullptr;
     uint32_t j = 0;
 #pragma unroll 1
-    for (; j + 8 <= a.draws; j += 8) {
+    for (; a.draws - j >= 8; j += 8) {  // j <= draws: no wrap near 2^32
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         x = mcd::lcg_step(x, g, c);
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kDrawBlock, SEED == kStride ? 4 : 1) draw_dige
     } else {
       uint32_t j = 0;
 #pragma unroll 1
-      for (; j + 16 <= draws; j += 16) {
+      for (; draws - j >= 16; j += 16) {  // j <= draws: no wrap near 2^32
 #pragma unroll
         for (int t = 0; t < 16; t += 2) {
 #pragma unroll
