@@ -314,6 +314,9 @@ def main():
                 "traffic_unit": "bytes per launch (ncu dram read+write)",
                 "peak_note": f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {RECIPE_SM_MAX_MHZ:.0f} MHz",
                 "ops_per_draw": OPS_PER_DRAW}
+    if DRAW_KERNEL_TRAFFIC_BYTES is None:
+        roofline["traffic_note"] = ("no ncu capture of the kernel as built (launch bounds changed since); "
+                                    "the capture before measured 1.013e9 B per launch, the 1 GiB of results")
 
     # End to end through the public call: every final state and digest is
     # copied to pinned host memory inside the timed region, every step.  The
