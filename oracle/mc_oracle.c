@@ -81,20 +81,33 @@ uint64_t or_stride_seed(uint64_t x0, uint64_t q, uint64_t k, uint32_t m, uint64_
 }
 
 /* ---------------------------------------------------------------------------
- * Section 4, Listing 1: the modified murmur_hash64a, all values uint64_t with
- * wrapping multiplication.  READING: "utint64_t" is uint64_t; 8*M wraps.
+ * Section 4, Listing 1; Eq. (3): the hash of a key k under a parent seed s.
+ * It is built from one mixing map on 64-bit words,
+ *   mix(v) = p XOR floor(p / 2^47),   p = v * M mod 2^64,
+ * with M the multiplier the listing prints.  The seed enters as
+ * a = mix(s XOR (8 M mod 2^64)), the key as b = mix(k) * M mod 2^64, and the
+ * hash is mix(a XOR b).  READING: every value is an unsigned 64-bit word and
+ * every product is taken mod 2^64; here each product is formed exactly in
+ * 128 bits and reduced by keeping its low word, and the shift is logical.
  * ------------------------------------------------------------------------- */
 
 #define OR_MURMUR_M 0xC6A4A7935BD1E995ULL
 
-uint64_t or_subhash(uint64_t x) {
-    uint64_t xm = x * OR_MURMUR_M;
-    return xm ^ (xm >> 47);
+static uint64_t or_mulmod64(uint64_t a, uint64_t b) {
+    const unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    return (uint64_t)(p & (unsigned __int128)UINT64_MAX);
+}
+
+/* mix(v); exported under the listing's name for the tests. */
+uint64_t or_subhash(uint64_t v) {
+    const uint64_t p = or_mulmod64(v, OR_MURMUR_M);
+    return p ^ (p >> 47);
 }
 
 uint64_t or_hash(uint64_t k, uint64_t s) {
-    uint64_t seed_hash = or_subhash(s ^ (8ULL * OR_MURMUR_M));
-    return or_subhash(seed_hash ^ (or_subhash(k) * OR_MURMUR_M));
+    const uint64_t a = or_subhash(s ^ or_mulmod64(8, OR_MURMUR_M));
+    const uint64_t b = or_mulmod64(or_subhash(k), OR_MURMUR_M);
+    return or_subhash(a ^ b);
 }
 
 /* Eq. (3) S_k = hash(k, s), and Eq. (4) S_{i,j} = hash(j, hash(i, s)).

@@ -56,8 +56,11 @@ __host__ __device__ __forceinline__ Affine skip_map(uint64_t g, uint64_t c, uint
   return acc;
 }
 
-// Listing 1: subhash(x) = (xM) ^ ((xM) >> 47);
-// hash(k, s) = subhash(subhash(s ^ 8M) ^ (subhash(k) * M)).
+// Section 4, Listing 1 and Eq. 3: one mixing step multiplies by the murmur
+// constant (mod 2^64) and folds the product's top 17 bits into its low bits;
+// the hash mixes the key, multiplies it by the constant again, combines it by
+// XOR with the mixed seed (the seed first XORed with 8 times the constant)
+// and mixes the result once more.
 __host__ __device__ __forceinline__ uint64_t subhash(uint64_t x) {
   const uint64_t t = x * kMurmurM;
   return t ^ (t >> 47);
