@@ -80,6 +80,41 @@ MC_API int mc_ctx_create(mc_ctx** out, int device);
 /* Frees the context and its device memory (synchronises the device). */
 MC_API void mc_ctx_destroy(mc_ctx* ctx);
 
+/* Bounds on the waits of mc_transport_run under this context (failure
+ * detection; the paper has no counterpart).  Each bound turns a wait that
+ * would not end into an error status instead of a hang; the defaults are
+ * far above anything a valid run needs, and lowering them exists to test
+ * the give-up paths.  Every field is taken literally (0 is a bound of 0).
+ *   pool_lock_attempts  slab history kernel: attempts a warp makes at its
+ *                       block's compaction-pool lock before it gives up
+ *                       (default 2^20).  A warp that gives up skips the
+ *                       hand-over; one that is leaving counts what the pool
+ *                       may still hold in MC_C_DROPPED, which mc_tally_read
+ *                       reports as MC_ERR_CAPACITY.  0: no warp ever takes
+ *                       the lock, so no particle moves (tallies unchanged).
+ *   box_generations     generations of weight-window children the host
+ *                       follows before MC_ERR_TIMEOUT (default 10000).
+ *   pulse_generations   generations of overflowed pulse secondaries (hash
+ *                       modes) before MC_ERR_TIMEOUT (default 100000).
+ *   event_iterations    iterations of the event-based schedules (slab, and
+ *                       box per generation) before MC_ERR_TIMEOUT; rounded
+ *                       up to whole batches of iterations.  UINT64_MAX (the
+ *                       default) derives the bound from the event cap and
+ *                       the history count.
+ * A run that gave up leaves the tally partial; the context stays usable. */
+typedef struct {
+    uint32_t pool_lock_attempts;
+    uint32_t box_generations;
+    uint32_t pulse_generations;
+    uint32_t reserved; /* must be 0 */
+    uint64_t event_iterations;
+} mc_limits;
+
+/* Sets the context's bounds (NULL restores the defaults) or reads them.
+ * Errors: MC_ERR_ARG (ctx NULL, reserved != 0, out NULL). */
+MC_API int mc_ctx_set_limits(mc_ctx* ctx, const mc_limits* limits);
+MC_API int mc_ctx_get_limits(const mc_ctx* ctx, mc_limits* out);
+
 /* ---------------------------------------------------------- hash seeding
  * Section 4, Listing 1 and Eq. (3): d_states[i] = hash(key_begin + i,
  * parent_seed) mod 2^m, where hash is the modified murmur_hash64a of
@@ -285,21 +320,31 @@ MC_API int mc_autotune(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
 
 /* The slab transport of mc_transport_run for callers that cannot allocate
  * device memory (the paper has no counterpart; this is a deployment aid).
- * mc_transport_run needs an mc_ctx, and creating one calls cudaMalloc;
- * code running under CUDA graph capture, code whose device memory belongs to
- * another allocator, and code that must not grow its footprint after
+ * mc_transport_run needs an mc_ctx, and creating one calls cudaMalloc.  Code
+ * whose device memory belongs to another allocator (a framework's caching
+ * allocator, a fixed pool that accounts for every byte) and code that must
+ * not grow its footprint or take cudaMalloc's implicit synchronisation after
  * start-up cannot make that call.  This entry point allocates nothing: its
  * scratch (work ticket and device problem list) is one fixed __device__
- * array inside libmc, present on every device that loads the library until
- * the process exits.
- *   - At most 256 problems per call (MC_ERR_ARG beyond that); the
- *     history-based schedule only (MC_SCHED_EVENT is MC_ERR_ARG).
- *   - Same arguments, results and errors as mc_transport_run otherwise; the
- *     caller still owns and passes the tally buffers.
+ * array inside libmc, about 41 KiB, present on every device that loads the
+ * library until the process exits.
+ *   - Slab problems only, at most 256 per call, the history-based schedule
+ *     only (box or pulse problems, more problems and MC_SCHED_EVENT are
+ *     MC_ERR_ARG, each with its own message); every other argument is
+ *     checked as by mc_transport_run, with the same errors.
+ *   - The caller still owns and passes the tally buffers; the results are
+ *     the same bits as mc_transport_run's.  Launch shape: the same default
+ *     block and chunk; launches of several problems compute bin edges on the
+ *     fly instead of reading per-problem edge tables (which would need
+ *     scratch growing with the bin count), so they can run slower.
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make it before any stream capture starts.
- *   - All calls share the array: calls whose GPU work overlaps (other
- *     streams, other host threads) race and must be serialised. */
+ *     that device current); make it before any stream capture starts.  The
+ *     address is kept for the life of the process: resetting the device
+ *     after the first call is not supported.
+ *   - All calls share the array, which keeps the last call's contents (each
+ *     call rewrites the problem list and zeroes the ticket first): calls
+ *     whose GPU work overlaps (other streams, other host threads) race and
+ *     must be serialised. */
 MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
                                    const mc_run_config* config, const mc_tally* tally, void* stream);
 
@@ -335,8 +380,11 @@ MC_API int mc_log1m_device(const double* d_u, double* d_out, uint64_t n, int whi
 
 /* Diagnostics of the fp64 steps the transport computes on the integer pipes
  * (no counterpart in the paper): mc_recip_rn(y) is 1/y rounded to nearest
- * even, exactly as IEEE division, built from an fp32 estimate, two integer
- * Newton steps and an exact remainder (host evaluation of the device code);
+ * even, exactly as IEEE division: a table of 2^63/F (F the left end of the
+ * mantissa's cell among 1024, the flight logarithm's table), 1/(1 + r)
+ * through r^5 by Horner's rule on non-negative fixed point, an exact
+ * remainder check and the rounding; IEEE division for zero, subnormal or
+ * huge operands (host evaluation of the device code);
  * mc_recip_rn_device writes d_out[i] = 1/d_y[i] with it (which = 0) or with
  * the CUDA division (which = 1); mc_two_u_minus_1(n) is 2u - 1 for the
  * uniform u = n 2^-53 (n < 2^53; 0 otherwise).  Errors: MC_ERR_ARG,

@@ -22,7 +22,7 @@ from ._ffi import (  # noqa: F401  (re-exported names)
     COUNT_NAMES, MC_FP32_GUARDED, MC_FP64, MC_GEOM_BOX, MC_GEOM_PULSE, MC_GEOM_SLAB, MC_NCOUNT,
     MC_SCHED_AUTO, mc_pulse_spec,
     MC_SCHED_EVENT, MC_SCHED_HISTORY, MC_SEED_HASH, MC_SEED_HASH_HIER, MC_SEED_STRIDE,
-    MC_SRC_BEAM, MC_SRC_ISOTROPIC, McError, mc_box_spec, mc_lcg, mc_problem, mc_run_config,
+    MC_SRC_BEAM, MC_SRC_ISOTROPIC, McError, mc_box_spec, mc_lcg, mc_limits, mc_problem, mc_run_config,
     mc_seed_spec, mc_tally,
 )
 
@@ -85,6 +85,17 @@ def mc_ctx_create(device: int = 0) -> Context:
 
 def mc_ctx_destroy(ctx: Context) -> None:
     ctx.close()
+
+
+def mc_ctx_set_limits(ctx: Context, limits: Optional[mc_limits] = None) -> None:
+    """Bounds on the waits of a run under ctx (None restores the defaults)."""
+    _ffi.check(lib().mc_ctx_set_limits(ctx.handle, C.byref(limits) if limits is not None else None))
+
+
+def mc_ctx_get_limits(ctx: Context) -> mc_limits:
+    out = mc_limits()
+    _ffi.check(lib().mc_ctx_get_limits(ctx.handle, C.byref(out)))
+    return out
 
 
 def mc_last_error() -> str:

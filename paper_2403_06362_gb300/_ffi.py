@@ -34,6 +34,7 @@ EXPORTED = [
     "mc_lcg_draw", "mc_transport_run", "mc_tally_read", "mc_hash64", "mc_normality",
     "mc_transport_run_static", "mc_autotune", "mc_log1m", "mc_log1m_device", "mc_recip_rn",
     "mc_two_u_minus_1", "mc_recip_rn_device", "mc_llrint_nonneg", "mc_d_lt", "mc_mul_small",
+    "mc_ctx_set_limits", "mc_ctx_get_limits",
 ]
 
 
@@ -96,6 +97,13 @@ class mc_run_config(C.Structure):
     ]
 
 
+class mc_limits(C.Structure):
+    _fields_ = [
+        ("pool_lock_attempts", C.c_uint32), ("box_generations", C.c_uint32),
+        ("pulse_generations", C.c_uint32), ("reserved", C.c_uint32), ("event_iterations", C.c_uint64),
+    ]
+
+
 class mc_tally(C.Structure):
     _fields_ = [
         ("d_bins", C.c_void_p), ("n_slots", C.c_uint64), ("d_counts", C.c_void_p),
@@ -114,6 +122,8 @@ def _load():
         "mc_last_error": (C.c_char_p, []),
         "mc_ctx_create": (i32, [C.POINTER(C.c_void_p), i32]),
         "mc_ctx_destroy": (None, [P]),
+        "mc_ctx_set_limits": (i32, [P, C.POINTER(mc_limits)]),
+        "mc_ctx_get_limits": (i32, [P, C.POINTER(mc_limits)]),
         "mc_seed_hash": (i32, [P, C.POINTER(mc_lcg), u64, u64, u64, P, P]),
         "mc_seed_stride": (i32, [P, C.POINTER(mc_lcg), u64, u64, u64, u64, P, P]),
         "mc_lcg_draw": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_seed_spec), u64, P, u64, u32, P, P, P]),

@@ -289,6 +289,8 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
   L.block = cfg->block ? (int)std::min<uint32_t>(cfg->block, 256u) : 256;
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
+  L.max_generations = ctx->limits.box_generations;
+  L.event_iterations = ctx->limits.event_iterations;
   if (cfg->schedule == MC_SCHED_EVENT) {
     const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.total, 1), 1u << 20);
     st = ctx->bank.reserve(mci::box_bank_bytes(cap));
@@ -306,6 +308,56 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
 }
 
 }  // namespace
+
+namespace mci {
+
+int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t* total) {
+  return ::check_problems(p, n, t, total);
+}
+
+int check_run_config(const mc_run_config* cfg, const char* who) {
+  if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
+      (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512)) || cfg->stack_depth > 256 ||
+      cfg->reserved2 != 0) {
+    set_error("%s: bad run config (schedule/precision/tally_mode/block/stack_depth)", who);
+    return MC_ERR_ARG;
+  }
+  return MC_OK;
+}
+
+// About four grabs per resident warp: fine-grained enough to balance
+// long-tailed histories, coarse enough that lanes rarely change problem in
+// a batched launch; within [32, 1024].
+uint32_t slab_default_chunk(uint64_t total, int num_sms) {
+  return (uint32_t)std::min<uint64_t>(1024, std::max<uint64_t>(32, total / ((uint64_t)num_sms * 256)));
+}
+
+// 256 threads, except that a run too small to give every SM a block of 256
+// is spread over all SMs in smaller blocks: its time is the latency of its
+// longest warps, which run faster with fewer warps per sub-partition.
+int slab_default_block(uint64_t total, uint32_t chunk, int num_sms) {
+  const uint64_t warps = (total + chunk - 1) / chunk;
+  if (warps * 32 < (uint64_t)num_sms * 256)
+    return (int)std::max<uint64_t>(32, 32 * std::max<uint64_t>(1, warps / (uint64_t)num_sms));
+  return 256;
+}
+
+// Slots staged in shared memory: all of them (tally_mode 1, an error when
+// they do not fit beside 2 KiB of the kernel's own static shared memory),
+// none (mode 2), or all when at most 8192 (64 KiB; mode 0, "auto").
+int slab_staged_slots(const mc_run_config* cfg, const mc_tally* tally, size_t smem_optin, const char* who,
+                      uint32_t* slots) {
+  const bool fits = tally->n_slots * 8u + 2048u <= smem_optin;
+  if (cfg->tally_mode == 1 && !fits) {
+    set_error("%s: %llu tally slots do not fit in shared memory", who, (unsigned long long)tally->n_slots);
+    return MC_ERR_ARG;
+  }
+  const bool stage = cfg->tally_mode == 1 || (cfg->tally_mode == 0 && tally->n_slots <= 8192u);
+  *slots = stage ? (uint32_t)tally->n_slots : 0u;
+  return MC_OK;
+}
+
+}  // namespace mci
 
 extern "C" {
 
@@ -337,6 +389,28 @@ MC_API int mc_ctx_create(mc_ctx** out, int device) {
     return st;
   }
   *out = c;
+  return MC_OK;
+}
+
+MC_API int mc_ctx_set_limits(mc_ctx* ctx, const mc_limits* limits) {
+  if (!ctx) {
+    mci::set_error("mc_ctx_set_limits: ctx is NULL");
+    return MC_ERR_ARG;
+  }
+  if (limits && limits->reserved != 0) {
+    mci::set_error("mc_ctx_set_limits: reserved field must be 0");
+    return MC_ERR_ARG;
+  }
+  ctx->limits = limits ? *limits : mci::default_limits();
+  return MC_OK;
+}
+
+MC_API int mc_ctx_get_limits(const mc_ctx* ctx, mc_limits* out) {
+  if (!ctx || !out) {
+    mci::set_error("mc_ctx_get_limits: NULL argument");
+    return MC_ERR_ARG;
+  }
+  *out = ctx->limits;
   return MC_OK;
 }
 
@@ -384,12 +458,8 @@ int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uin
   if (st != MC_OK) return st;
   st = check_problems(problems, n_problems, tally, total);
   if (st != MC_OK) return st;
-  if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
-      (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512)) || cfg->stack_depth > 256 ||
-      cfg->reserved2 != 0) {
-    mci::set_error("mc_transport_run: bad run config (schedule/precision/tally_mode/block/stack_depth)");
-    return MC_ERR_ARG;
-  }
+  st = mci::check_run_config(cfg, "mc_transport_run");
+  if (st != MC_OK) return st;
   const uint64_t rb = cfg->range_begin, re = cfg->range_end == 0 ? *total : cfg->range_end;
   if (rb > re || re > *total) {
     mci::set_error("mc_transport_run: range [%llu, %llu) outside the %llu histories", (unsigned long long)rb,
@@ -412,39 +482,23 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   L.d_probs = ctx->problems.ptr;
   L.d_tables = slab_tables_of(ctx, n_problems);
   L.n_problems = n_problems;
-  // Default chunk: about four grabs per resident warp (fine-grained enough to
-  // balance long-tailed histories, coarse enough that lanes rarely change
-  // problem in a batched launch), within [32, 1024].
-  L.chunk = cfg->chunk ? cfg->chunk
-                       : (uint32_t)std::min<uint64_t>(1024, std::max<uint64_t>(32, (re - rb) / ((uint64_t)ctx->num_sms * 256)));
+  L.chunk = cfg->chunk ? cfg->chunk : mci::slab_default_chunk(re - rb, ctx->num_sms);
   L.range_begin = rb;
   L.total = re - rb;
   L.d_ticket = ticket;
   L.tally = tally;
   L.lcg = *lcg;
   L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 40);
-  const uint64_t smem_cap = 8192;  // slots (64 KiB) staged in shared memory under "auto"
-  // (2 KiB left for the kernel's own static shared memory)
-  const bool fits = tally->n_slots * 8u + 2048u <= ctx->smem_optin;
-  if (cfg->tally_mode == 1 && !fits) {
-    mci::set_error("mc_transport_run: %llu tally slots do not fit in shared memory",
-                   (unsigned long long)tally->n_slots);
-    return MC_ERR_ARG;
-  }
-  const bool stage = cfg->tally_mode == 1 || (cfg->tally_mode == 0 && tally->n_slots <= smem_cap);
-  L.smem_slots = stage ? (uint32_t)tally->n_slots : 0u;
+  uint32_t slots = 0;
+  int st = mci::slab_staged_slots(cfg, tally, ctx->smem_optin, "mc_transport_run", &slots);
+  if (st != MC_OK) return st;
+  L.smem_slots = slots;
   L.f32 = cfg->precision == MC_FP32_GUARDED;
-  L.block = cfg->block ? (int)cfg->block : 256;
-  if (!cfg->block) {
-    // A run too small to give every SM a block of 256 threads is spread over
-    // all SMs in smaller blocks: its time is the latency of its longest warps,
-    // which run faster with fewer warps per sub-partition.
-    const uint64_t warps = (L.total + L.chunk - 1) / L.chunk;
-    if (warps * 32 < (uint64_t)ctx->num_sms * 256)
-      L.block = (int)std::max<uint64_t>(32, 32 * std::max<uint64_t>(1, warps / (uint64_t)ctx->num_sms));
-  }
+  L.block = cfg->block ? (int)cfg->block : mci::slab_default_block(L.total, L.chunk, ctx->num_sms);
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
+  L.pool_lock_attempts = ctx->limits.pool_lock_attempts;
+  L.event_iterations = ctx->limits.event_iterations;
   *out = L;
   return MC_OK;
 }
@@ -468,6 +522,7 @@ int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, u
                         tally->d_hist_draws};
   key = fnv(key, ptrs, sizeof ptrs);
   key = fnv(key, cfg, sizeof *cfg);
+  key = fnv(key, &ctx->limits, sizeof ctx->limits);  // the lock bound is a kernel argument
   key = fnv(key, lcg, sizeof *lcg);
   key = fnv(key, &n_problems, sizeof n_problems);
   key = fnv(key, &bytes, sizeof bytes);
@@ -544,6 +599,7 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     P.num_sms = ctx->num_sms;
     P.stack_depth = cfg->stack_depth ? cfg->stack_depth : 256u;
     P.seeding = problems[0].seeding;
+    P.max_generations = ctx->limits.pulse_generations;
     if (problems[0].seeding != MC_SEED_STRIDE) {
       // overflow bank of 2^20 secondaries (32 MiB per generation bank)
       P.ovf_cap = 1ull << 20;

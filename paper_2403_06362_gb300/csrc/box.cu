@@ -278,8 +278,8 @@ int run_box_history(const mci::BoxLaunch& L, cudaStream_t s) {
         return MC_ERR_CAPACITY;
       }
       if (made == 0) break;
-      if (gen > 10000) {
-        mci::set_error("box transport: more than 10000 generations of children");
+      if ((uint32_t)gen > L.max_generations) {
+        mci::set_error("box transport: more than %u generations of children", L.max_generations);
         return MC_ERR_TIMEOUT;
       }
       const int nxt = cur ^ 1;

@@ -401,8 +401,10 @@ int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return mci::cuda_status(e, "cudaGraphInstantiate(box event batch)");
   }
-  const uint64_t max_batches = (std::min<uint64_t>(L.event_cap, 1ull << 36) * 4 + 64) / kIter +
-                               (a.total / a.b.cap + 2) * 4;
+  uint64_t max_batches = (std::min<uint64_t>(L.event_cap, 1ull << 36) * 4 + 64) / kIter +
+                         (a.total / a.b.cap + 2) * 4;
+  if (L.event_iterations != ~0ull)  // a caller's bound (mc_limits), in whole batches
+    max_batches = L.event_iterations / kIter + (L.event_iterations % kIter != 0);
   int st = MC_OK;
   for (uint64_t batch = 0;; ++batch) {
     if (batch == max_batches) {
@@ -474,8 +476,8 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
         return MC_ERR_CAPACITY;
       }
       if (made == 0) break;
-      if (gen > 10000) {
-        mci::set_error("box event schedule: more than 10000 generations");
+      if ((uint32_t)gen > L.max_generations) {
+        mci::set_error("box event schedule: more than %u generations", L.max_generations);
         return MC_ERR_TIMEOUT;
       }
       const int nxt = cur ^ 1;

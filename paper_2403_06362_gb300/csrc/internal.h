@@ -27,6 +27,19 @@ int cuda_status(cudaError_t e, const char* what);
 // Validates an mc_lcg; fills `m`, `mask`.  Returns MC_OK or MC_ERR_ARG.
 int check_lcg(const mc_lcg* lcg);
 
+// Validates the problems of one mc_transport_run call against the tally and
+// returns their total history count (MC_ERR_ARG with a message otherwise).
+int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t* total);
+// Validates the fields of a run config; `who` prefixes the message.
+int check_run_config(const mc_run_config* cfg, const char* who);
+// Slab history launch defaults: histories per warp grab and block size.
+uint32_t slab_default_chunk(uint64_t total, int num_sms);
+int slab_default_block(uint64_t total, uint32_t chunk, int num_sms);
+// Tally slots staged in shared memory for cfg->tally_mode (MC_ERR_ARG when
+// mode 1 asks for more than fits).
+int slab_staged_slots(const mc_run_config* cfg, const mc_tally* tally, size_t smem_optin, const char* who,
+                      uint32_t* slots);
+
 // Device scratch owned by a context.  Sizes only grow, and only outside
 // the launch of a run (never inside a captured region).
 struct DeviceBuf {
@@ -35,6 +48,17 @@ struct DeviceBuf {
   int reserve(size_t want);  // grows with cudaMalloc; contents not kept
   void release();
 };
+
+// Default bounds on the waits of a run (mc_limits).
+inline mc_limits default_limits() {
+  mc_limits l{};
+  l.pool_lock_attempts = 1u << 20;
+  l.box_generations = 10000u;
+  l.pulse_generations = 100000u;
+  l.reserved = 0u;
+  l.event_iterations = ~0ull;
+  return l;
+}
 
 // Instantiated launch graphs of the history schedule, keyed by launch shape.
 struct GraphCache {
@@ -47,6 +71,7 @@ struct mc_ctx {
   int device = 0;
   int num_sms = 0;
   size_t smem_optin = 0;  // max dynamic shared memory per block (opt-in)
+  mc_limits limits = mci::default_limits();  // bounds on the waits of a run
   // Small scratch: work tickets, status word, count staging.
   mci::DeviceBuf scratch;
   // Device copy of the problem list and per-problem derived constants.

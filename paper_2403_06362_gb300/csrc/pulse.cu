@@ -387,8 +387,8 @@ int pulse_run(const PulseLaunch& L, cudaStream_t s) {
     MC_TRY_CUDA(cudaStreamSynchronize(s));
     const uint64_t made = std::min<uint64_t>(*L.h_count, L.ovf_cap);
     if (made == 0) break;
-    if (gen > 100000) {
-      set_error("pulse transport: more than 100000 generations of overflowed secondaries");
+    if ((uint32_t)gen > L.max_generations) {
+      set_error("pulse transport: more than %u generations of overflowed secondaries", L.max_generations);
       return MC_ERR_TIMEOUT;
     }
     PulseArgs b = a;

@@ -495,8 +495,8 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
                                   s));
       MC_TRY_CUDA(cudaStreamSynchronize(s));
       if (*L.base.h_count == 0) break;
-      if (gen > 100000) {
-        set_error("pulse census: more than 100000 generations of overflowed secondaries");
+      if ((uint32_t)gen > L.base.max_generations) {
+        set_error("pulse census: more than %u generations of overflowed secondaries", L.base.max_generations);
         return MC_ERR_TIMEOUT;
       }
       CensusArgs b = a;

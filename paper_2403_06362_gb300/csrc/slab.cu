@@ -84,6 +84,7 @@ struct RunArgs {
   const double* tables; // else per-problem edge and width tables in global memory (nullable)
   uint32_t donate_max;  // a warp with 1..donate_max live lanes after the ticket ran out donates them
   uint32_t pool_cap;    // particles the block's shared pool holds (0: no compaction)
+  uint32_t lock_attempts;  // attempts at the pool lock before a warp gives up
 };
 
 // In-block compaction of the long-chain tail.  Once the ticket runs out,
@@ -101,8 +102,8 @@ struct PoolCtl {
   int lock, n, active, pad;
 };
 
-__device__ __forceinline__ bool pool_lock(int* lk) {
-  for (int i = 0; i < (1 << 20); ++i)
+__device__ __forceinline__ bool pool_lock(int* lk, uint32_t attempts) {
+  for (uint32_t i = 0; i < attempts; ++i)
     if (atomicCAS(lk, 0, 1) == 0) {
       __threadfence_block();
       return true;
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
       if (dead != 0u && hint_n > 0) {
         int k = 0, n = 0, ok = 0;
         if (lane == 0) {
-          ok = pool_lock(&ctl.lock);
+          ok = pool_lock(&ctl.lock, a.lock_attempts);
           if (ok) {
             n = vc.n;
             k = min(n, __popc(dead));
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
       if (nlive == 0 || (nlive <= (int)a.donate_max && hint_active > 1 && hint_n + nlive <= (int)a.pool_cap)) {
         int go = 0, n = 0;
         if (lane == 0) {
-          if (pool_lock(&ctl.lock)) {
+          if (pool_lock(&ctl.lock, a.lock_attempts)) {
             n = vc.n;
             if (nlive == 0 ? n == 0 : (vc.active > 1 && n + nlive <= (int)a.pool_cap)) {
               vc.n = n + nlive;
@@ -484,6 +485,7 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
   // holds what every other warp of the block could hand over
   a.donate_max = 12;
   a.pool_cap = L.block >= 64 ? (uint32_t)((L.block >> 5) - 1) * a.donate_max : 0u;
+  a.lock_attempts = L.pool_lock_attempts;
   if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
   return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
 }

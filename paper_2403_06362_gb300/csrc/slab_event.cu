@@ -453,7 +453,9 @@ int slab_event_run(const SlabLaunch& L, void* d_bank, uint32_t cap, unsigned int
   // Every iteration flies each live particle once, so the longest history
   // bounds the iteration count; the cap below is a safety net only.
   const uint64_t max_iters = std::min<uint64_t>(L.event_cap, 1ull << 36) * 2 + (L.total / cap + 2) * 4 + 64;
-  const uint64_t max_batches = max_iters / kIterPerBatch + 2;
+  uint64_t max_batches = max_iters / kIterPerBatch + 2;
+  if (L.event_iterations != ~0ull)  // a caller's bound (mc_limits), in whole batches
+    max_batches = L.event_iterations / kIterPerBatch + (L.event_iterations % kIterPerBatch != 0);
   if (L.lcg.m == 63) {
     return L.f32 ? run_event<63, true>(a, grid, capture_stream, h_done, max_batches, s)
                  : run_event<63, false>(a, grid, capture_stream, h_done, max_batches, s);

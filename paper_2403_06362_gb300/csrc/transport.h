@@ -24,6 +24,8 @@ struct SlabLaunch {
   const void* d_tables = nullptr;  // per-problem edge and width tables (nullable; see slab_prep)
   bool f32;
   int block, blocks_per_sm, num_sms;
+  uint32_t pool_lock_attempts = 1u << 20;  // compaction-pool lock (mc_limits)
+  uint64_t event_iterations = ~0ull;       // event schedule bound (mc_limits; ~0: derived)
 };
 
 size_t slab_dev_size();
@@ -68,6 +70,8 @@ struct BoxLaunch {
   uint32_t bank_cap;
   unsigned int* h_done;
   cudaStream_t capture_stream;
+  uint32_t max_generations = 10000u;  // child generations (mc_limits)
+  uint64_t event_iterations = ~0ull;  // per generation (mc_limits; ~0: derived)
 };
 
 // One run of the pulse problem (pulse.cu).
@@ -90,6 +94,7 @@ struct PulseLaunch {
   void* d_ovf;
   uint64_t ovf_cap;
   unsigned long long* h_count;
+  uint32_t max_generations = 100000u;  // overflow generations (mc_limits)
 };
 size_t pulse_ovf_bytes(uint64_t cap);
 

@@ -62,6 +62,10 @@ def test_argument_errors_are_reported_without_a_gpu(mc):
     t = mc.mc_tally()
     assert lib.mc_transport_run(C.c_void_p(1), C.byref(lcg), None, 0, C.byref(cfg), C.byref(t), None) \
         == mc._ffi.MC_ERR_ARG
+    # wait bounds: no context
+    lim = mc.mc_limits()
+    assert lib.mc_ctx_set_limits(None, C.byref(lim)) == mc._ffi.MC_ERR_ARG
+    assert lib.mc_ctx_get_limits(None, C.byref(lim)) == mc._ffi.MC_ERR_ARG
 
 
 def test_host_hash_matches_oracle(mc, oracle):
