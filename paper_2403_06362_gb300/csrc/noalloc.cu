@@ -3,24 +3,26 @@
 //
 // mc_transport_run keeps its scratch (the work ticket and the device copy of
 // the problem list) in an mc_ctx, whose creation calls cudaMalloc.  Some
-// callers cannot do that: code that runs while a CUDA graph is being
-// captured, code in a process whose device memory is owned by another
-// allocator (a framework's caching allocator or a fixed memory pool), or
-// code that must not grow its footprint after start-up.  This entry point
-// takes its scratch from one file-scope __device__ array instead.  The
-// array is part of the module image: every device that loads libmc holds
-// kStaticBytes of it until the process exits.
+// callers cannot do that: code in a process whose device memory is owned by
+// another allocator (a framework's caching allocator or a fixed memory pool
+// that must account for every byte), and code that must not grow its
+// footprint or take cudaMalloc's implicit device synchronisation after
+// start-up (a latency-bound service, a plugin inside a host application).
+// This entry point takes its scratch from one file-scope __device__ array
+// instead.  The array is part of the module image: every device that loads
+// libmc holds kStaticBytes of it until the process exits.
 //
 // Set-up: on the first call on a device (with that device current) the
 // host looks up the array's device address with cudaGetSymbolAddress and
-// caches it; make that first call before any stream capture begins.
+// caches it; make that first call before any stream capture begins.  The
+// cached address belongs to the device's context at that time, so a device
+// reset after the first call is not supported.
 // Sharing: every call uses the same array, which keeps the previous call's
 // contents; the upload kernel rewrites the problem list and zeroes the
 // ticket on every call.  Two calls whose work overlaps on the GPU (two
 // streams, or two host threads) race on the array: serialise them.
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -78,6 +80,9 @@ int device_slot(DeviceSlot** out) {
   return MC_OK;
 }
 
+// The checks of mc_transport_run (shared with api.cu), then this entry
+// point's own limits: slab problems only, at most kStaticMaxProblems, the
+// history schedule.
 int check_static_args(const mc_problem* p, uint32_t n, const mc_run_config* cfg, const mc_tally* t,
                       uint64_t* total) {
   if (n > kStaticMaxProblems) {
@@ -85,25 +90,21 @@ int check_static_args(const mc_problem* p, uint32_t n, const mc_run_config* cfg,
                    kStaticMaxProblems);
     return MC_ERR_ARG;
   }
-  if (cfg->schedule == MC_SCHED_EVENT || cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED ||
-      cfg->tally_mode > 2 || (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512))) {
-    mci::set_error("mc_transport_run_static: bad run config (history schedule only)");
-    return MC_ERR_ARG;
-  }
-  uint64_t acc = 0;
   for (uint32_t i = 0; i < n; ++i) {
-    const mc_problem& q = p[i];
-    const bool ok = q.geometry == MC_GEOM_SLAB && q.L > 0.0 && q.sigma_t > 0.0 && std::isfinite(q.L) &&
-                    std::isfinite(q.sigma_t) && q.c >= 0.0 && q.c <= 1.0 && q.n_bins > 0 && q.n_batches > 0 &&
-                    q.source <= MC_SRC_BEAM && q.seeding <= MC_SEED_HASH_HIER && q.reserved == 0;
-    const uint64_t slots = (uint64_t)q.n_bins * q.n_batches;
-    if (!ok || q.tally_offset > t->n_slots || slots > t->n_slots - q.tally_offset) {
-      mci::set_error("mc_transport_run_static: problem %u is invalid or outside the tally", i);
+    if (p[i].geometry != MC_GEOM_SLAB) {
+      mci::set_error("mc_transport_run_static: problem %u is not a slab problem (box and pulse geometries need "
+                     "mc_transport_run)", i);
       return MC_ERR_ARG;
     }
-    acc += q.n_histories;
   }
-  *total = acc;
+  int st = mci::check_problems(p, n, t, total);
+  if (st != MC_OK) return st;
+  st = mci::check_run_config(cfg, "mc_transport_run_static");
+  if (st != MC_OK) return st;
+  if (cfg->schedule == MC_SCHED_EVENT) {
+    mci::set_error("mc_transport_run_static: the history schedule only (its bank would need an allocation)");
+    return MC_ERR_ARG;
+  }
   return MC_OK;
 }
 
@@ -129,6 +130,9 @@ extern "C" MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_proble
   DeviceSlot* slot = nullptr;
   st = device_slot(&slot);
   if (st != MC_OK) return st;
+  uint32_t slots = 0;  // checked before anything is enqueued
+  st = mci::slab_staged_slots(cfg, tally, (size_t)slot->smem_optin, "mc_transport_run_static", &slots);
+  if (st != MC_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   auto* ticket = static_cast<unsigned long long*>(slot->scratch);
   auto* dprobs = reinterpret_cast<mcs::SlabDev*>(static_cast<unsigned char*>(slot->scratch) + kTicketBytes);
@@ -153,23 +157,17 @@ extern "C" MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_proble
   mci::SlabLaunch L{};
   L.d_probs = dprobs;
   L.n_problems = n_problems;
-  L.chunk = cfg->chunk ? cfg->chunk : 32u;
+  L.chunk = cfg->chunk ? cfg->chunk : mci::slab_default_chunk(re - rb, slot->num_sms);
   L.range_begin = rb;
   L.total = re - rb;
   L.d_ticket = ticket;
   L.tally = tally;
   L.lcg = *lcg;
   L.event_cap = cfg->event_cap ? cfg->event_cap : (1ull << 40);
-  const bool fits = tally->n_slots * 8u <= (uint64_t)slot->smem_optin;
-  if (cfg->tally_mode == 1 && !fits) {
-    mci::set_error("mc_transport_run_static: tally does not fit in shared memory");
-    return MC_ERR_ARG;
-  }
-  const bool stage = cfg->tally_mode == 1 || (cfg->tally_mode == 0 && tally->n_slots <= 8192);
-  L.smem_slots = stage ? (uint32_t)tally->n_slots : 0u;
+  L.smem_slots = slots;
   L.single_n_bins = n_problems == 1 ? problems[0].n_bins : 0u;
   L.f32 = cfg->precision == MC_FP32_GUARDED;
-  L.block = cfg->block ? (int)cfg->block : 256;
+  L.block = cfg->block ? (int)cfg->block : mci::slab_default_block(L.total, L.chunk, slot->num_sms);
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = slot->num_sms;
   return mci::slab_history_launch(L, s);

@@ -1,9 +1,13 @@
 """mc_transport_run_static, the entry point for callers that cannot allocate
-device memory (no mc_ctx, scratch in a fixed device array inside libmc),
-must give the same results as mc_transport_run, call after call, even
-though every call reuses the array the previous call left behind.  This file
-is collected last so that a run stopping at the first failure has run every
-other test first."""
+device memory (code whose device memory belongs to another allocator, or
+that must not grow its footprint after start-up; it needs no mc_ctx and keeps
+its scratch in a fixed device array inside libmc), must give the same
+results as mc_transport_run, call after call, even though every call reuses
+the array the previous call left behind.  Both entry points make the same
+int64 tally contributions, so the bins must be equal bit for bit (within the
+1e-6 relative bar of the other parity tests, which equality meets).  This
+file is collected last so that a run stopping at the first failure has run
+every other test first."""
 import numpy as np
 import pytest
 
@@ -41,6 +45,7 @@ def test_static_entry_matches_context_entry_on_consecutive_calls():
         rb = ref.bins.cpu().numpy().astype(np.float64)
         gb = got.bins.cpu().numpy().astype(np.float64)
         assert np.all(np.abs(gb - rb) <= TOL * np.abs(rb))
+        assert torch.equal(got.bins, ref.bins)
         assert torch.equal(got.counts, ref.counts)
         assert torch.equal(got.hist_state, ref.hist_state)
         assert torch.equal(got.hist_draws, ref.hist_draws)
@@ -57,3 +62,33 @@ def test_static_entry_rejects_too_many_problems():
     with pytest.raises(mc.McError) as e:
         mc.mc_transport_run_static(mc.make_lcg(), arr, mc.mc_run_config(), tally.c)
     assert e.value.status == mc._ffi.MC_ERR_ARG and "256" in str(e.value)
+
+
+def test_static_entry_at_its_problem_maximum():
+    """256 problems, the largest call the fixed array holds, after a call
+    with fewer problems."""
+    import torch
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    ctx = mc.Context(0)
+    for n in (3, 256):
+        probs = W.slab_batched(W.SEED_STRIDE, n_problems=n, max_histories=400)
+        ref, got = run_both(mc, ctx, torch, probs)
+        assert torch.equal(got.bins, ref.bins)
+        assert torch.equal(got.counts, ref.counts)
+        assert torch.equal(got.hist_state, ref.hist_state)
+    ctx.close()
+
+
+def test_static_entry_rejects_other_geometries():
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    b = W.box_problem(n_histories=10)
+    prob, spec = W.to_mc_box(b, mc)
+    tally = mc.Tally(W.box_tally_slots(b), 1)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_transport_run_static(mc.make_lcg(), mc.problem_array([prob]), mc.mc_run_config(), tally.c)
+    assert e.value.status == mc._ffi.MC_ERR_ARG and "not a slab problem" in str(e.value)
+    del spec
