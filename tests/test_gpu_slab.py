@@ -220,6 +220,49 @@ def test_long_chains_full_size_sampled(env, oracle):
     assert int(c[0]) == int(c[3]) + int(c[5]) + int(c[6])
 
 
+@pytest.mark.parametrize("seeding", [W.SEED_HASH, W.SEED_STRIDE])
+def test_long_chains_tally_parity_on_every_batch(env, oracle, seeding):
+    """The full long-chain slab (L = 200, c = 0.9999, 200 bins, 20 batches of
+    5·10^4 ids): the first 1000 ids of every batch, run through
+    range_begin/range_end into one tally (20 accumulating calls), against
+    the oracle on the same ids.  Every one of the 20 x 200 slots within 1e-6
+    relative, counters exact, per-history final states and draw counts
+    exact.  The GPU's flight logarithm and the oracle's differ by one ulp on
+    about 0.2 % of inputs; a leak/collide decision flipped by that would show
+    as a history whose final state differs, and is reported by id."""
+    mc, ctx, torch = env
+    probs = W.slab_long(seeding)
+    p = probs[0]
+    n, nbat, nb, per = p["n_histories"], p["n_batches"], p["n_bins"], 1000
+    tally = mc.Tally(W.tally_slots(probs), 1, n_histories=n)
+    cprobs = mc.problem_array([W.to_mc_problem(q, mc) for q in probs])
+    starts = [b * n // nbat for b in range(nbat)]
+    assert all((s0 * nbat) // n == b and ((s0 + per - 1) * nbat) // n == b for b, s0 in enumerate(starts))
+    for b, s0 in enumerate(starts):
+        cfg = mc.mc_run_config(range_begin=s0, range_end=s0 + per, accumulate=1 if b else 0)
+        mc.mc_transport_run(ctx, mc.make_lcg(), cprobs, cfg, tally.c)
+    torch.cuda.synchronize()
+    P = W.to_oracle_problem(p, oracle)
+    size = W.tally_slots(probs)
+    ot = np.zeros(size, dtype=np.int64)
+    oc = np.zeros(oracle.NCOUNT, dtype=np.uint64)
+    hs = tally.hist_state.cpu().numpy().view(np.uint64)
+    hd = tally.hist_draws.cpu().numpy().view(np.uint64)
+    flips = []
+    for s0 in starts:
+        r = oracle.slab_run(olcg(oracle), P, s0, s0 + per, tally=ot, counts=oc, per_history=True)
+        bad = np.nonzero((hs[s0:s0 + per] != r["hist_state"]) | (hd[s0:s0 + per] != r["hist_draws"]))[0]
+        flips += [s0 + int(i) for i in bad]
+    assert not flips, f"histories whose final state or draw count differ: {flips[:20]}"
+    got = tally.bins.cpu().numpy().reshape(nbat, nb)
+    exp = ot.reshape(nbat, nb)
+    assert np.count_nonzero(exp) == nbat * nb  # every slot scored: the comparison covers all 4000
+    assert_tally_close(got, exp)
+    gc = counts_of(tally, 1)[0]
+    assert np.array_equal(gc[:13], oc[:13]) and gc[13] == oc[13], (gc, oc)
+    assert int(gc[0]) == nbat * per
+
+
 def test_event_cap_reported(env):
     mc, ctx, torch = env
     p = W.slab_problem(200.0, 1.0, 0.9999, 500, 10, 1, W.SEED_HASH)
