@@ -37,20 +37,27 @@ METRIC = ("particle histories/sec and RNG draws/sec on 1 GB300 "
           "(hash vs stride, % int-pipe roofline)")
 N_STREAMS = 2**26
 DRAWS = 64
-# Operations per draw of the formulation in csrc/rng.cu (draw_digest_m63_kernel,
-# on the doubled state z = 2x): 64-bit multiply-add as IMAD.WIDE + 2 IMAD with
-# the increment folded in (3); normalising shift, one bfind (1); the 53 uniform
-# bits shifted into place as two words: funnel shift, shift, funnel shift,
-# shift (4); the shift summed for the exponent field (1, fp32 pipe); digest add,
-# one three-operand 64-bit add per two draws (1).  The exponent field and the
-# range check are folded into those sums.
-OPS_PER_DRAW = 10
+# Integer operations per draw, two counts.  OPS_PER_DRAW is the count the
+# hot-path table gives for one uniform of Eq. 1: the 64-bit multiply-add as
+# IMAD.WIDE + 2 IMAD with the increment folded in (3), and at least 8 integer
+# ALU operations to form the fp64 uniform (extract the 53 bits, count leading
+# zeros, normalising shift, exponent insert).  The headline fraction uses it.
+# OPS_PER_DRAW_KERNEL_FORM counts the summed form that csrc/rng.cu
+# (draw_digest_m63_kernel, on the doubled state z = 2x) runs: the multiply-add
+# (3); normalising shift, one bfind (1); the 53 uniform bits shifted into place
+# as two words (4); the shift summed for the exponent field (1, fp32 pipe);
+# digest add, one three-operand 64-bit add per two draws (1).  The exponent
+# field and the range check fold into those sums, so the form never builds the
+# fp64 value; both fractions are printed.
+OPS_PER_DRAW = 11
+OPS_PER_DRAW_KERNEL_FORM = 10
 E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 # DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
-# an ncu capture of the kernel as it is built (mean of the hash and stride
-# launches).  None: the launch bounds changed after the last capture, which
-# profiles/draw_digest_m63_kernel_rng_microbench.md summarises.
-DRAW_KERNEL_TRAFFIC_BYTES = None
+# an ncu capture of the kernel as built (mean of the hash and stride launches;
+# profiles/draw_digest_m63_kernel_rng_microbench.md).
+DRAW_KERNEL_TRAFFIC_BYTES = 1.013e9
+# Streams of the materialised-uniform leg (fp64 uniforms stored, draw-major).
+N_STREAMS_MATERIALISED = 2**22
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 
@@ -312,11 +319,11 @@ def main():
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": DRAW_KERNEL_TRAFFIC_BYTES,
                 "traffic_unit": "bytes per launch (ncu dram read+write)",
-                "peak_note": f"{props.multi_processor_count} SMs x 128 lane-ops/clk x {RECIPE_SM_MAX_MHZ:.0f} MHz",
-                "ops_per_draw": OPS_PER_DRAW}
-    if DRAW_KERNEL_TRAFFIC_BYTES is None:
-        roofline["traffic_note"] = ("no ncu capture of the kernel as built (launch bounds changed since); "
-                                    "the capture before measured 1.013e9 B per launch, the 1 GiB of results")
+                "peak_note": f"derived: {props.multi_processor_count} SMs x 128 lane-ops/clk x "
+                             f"{RECIPE_SM_MAX_MHZ:.0f} MHz (no measured integer peak exists)",
+                "ops_per_draw": OPS_PER_DRAW,
+                "ops_per_draw_kernel_form": OPS_PER_DRAW_KERNEL_FORM,
+                "frac_kernel_form": OPS_PER_DRAW_KERNEL_FORM * n * DRAWS / (launch_ms / 1e3) / peak}
 
     # End to end through the public call: every final state and digest is
     # copied to pinned host memory inside the timed region, every step.  The
@@ -367,6 +374,7 @@ def main():
               "ms_hash": statistics.mean(t_hash), "ms_stride": statistics.mean(t_str)}
     if not args.no_detail and rank == 0:
         detail.update(seeding_detail(mc, ctx, lcg, torch, dev, stream))
+        detail.update(materialised_detail(mc, ctx, lcg, torch, dev, stream, specs))
         detail.update(transport_detail(mc, ctx, lcg, torch, dev, stream, W))
 
     del st, dg, flush
@@ -467,6 +475,39 @@ def seeding_detail(mc, ctx, lcg, torch, dev, stream):
         res[f"seeds_per_s_{name}"] = n / (ms / 1e3)
         res[f"seed_{name}_hbm"] = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                                    "frac": gbs / peaks["hbm_gbs"], "peak_source": src}
+    return res
+
+
+def materialised_detail(mc, ctx, lcg, torch, dev, stream, specs):
+    """Mode (iii) of the microbenchmark: seeding plus 64 draws with every fp64
+    uniform stored (draw-major, u[j][i]) and the final states, for the first
+    2^22 of the 2^26 ids, hash- and stride-seeded.  HBM-store bound:
+    8 bytes per draw plus 8 per stream written."""
+    peaks, src = measured_peaks()
+    n = N_STREAMS_MATERIALISED
+    u = torch.empty(n * DRAWS, dtype=torch.float64, device=dev)
+    st = torch.empty(n, dtype=torch.int64, device=dev)
+    res = {}
+    for name, spec in zip(("hash", "stride"), specs):
+        for _ in range(3):
+            mc.mc_lcg_draw(ctx, lcg, spec, 0, st, n, DRAWS, u, None, stream)
+        ts = []
+        for _ in range(20):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mc.mc_lcg_draw(ctx, lcg, spec, 0, st, n, DRAWS, u, None, stream)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
+        nbytes = n * DRAWS * 8 + n * 8
+        gbs = nbytes / (ms / 1e3) / 1e9
+        res[f"materialised_uniforms_{name}"] = {
+            "streams": n, "draws_per_stream": DRAWS, "ms": ms, "draws_per_s": n * DRAWS / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "draw_kernel (uniforms stored)", "achieved": gbs,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                         "peak_source": src, "bytes_per_launch": nbytes}}
+    del u, st
     return res
 
 
