@@ -269,7 +269,12 @@ typedef struct {
                             /* a device overflow bank processed after the launch  */
                             /* (their streams depend only on their seeds, Eq. 5); */
                             /* stride mode counts them in MC_C_DROPPED            */
-    uint32_t reserved2;     /* must be 0                                           */
+    uint32_t tally_atomics; /* history-schedule kernels (slab, box, pulse, census  */
+                            /* phases): 0 = library default (1), 1 = one atomic   */
+                            /* per lane and contribution, 2 = warp-aggregated:    */
+                            /* the lanes adding to one slot together combine      */
+                            /* their values and one lane adds the sum.  The bits  */
+                            /* are the same either way; event schedules use 1.    */
 } mc_run_config;
 
 /* Counter block per problem: uint64_t[MC_NCOUNT], exact integers. */

@@ -93,7 +93,7 @@ class mc_run_config(C.Structure):
         ("chunk", C.c_uint32), ("blocks_per_sm", C.c_uint32), ("use_graph", C.c_uint32),
         ("accumulate", C.c_uint32), ("tally_mode", C.c_uint32),
         ("event_cap", C.c_uint64), ("range_begin", C.c_uint64), ("range_end", C.c_uint64),
-        ("stack_depth", C.c_uint32), ("reserved2", C.c_uint32),
+        ("stack_depth", C.c_uint32), ("tally_atomics", C.c_uint32),
     ]
 
 

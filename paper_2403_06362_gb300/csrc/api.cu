@@ -290,6 +290,7 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = ctx->num_sms;
   L.max_generations = ctx->limits.box_generations;
+  L.tally_agg = mci::tally_agg_of(cfg->tally_atomics, mci::kBoxAggDefault);
   L.event_iterations = ctx->limits.event_iterations;
   if (cfg->schedule == MC_SCHED_EVENT) {
     const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.total, 1), 1u << 20);
@@ -318,8 +319,8 @@ int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t*
 int check_run_config(const mc_run_config* cfg, const char* who) {
   if (cfg->schedule > MC_SCHED_AUTO || cfg->precision > MC_FP32_GUARDED || cfg->tally_mode > 2 ||
       (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block > 512)) || cfg->stack_depth > 256 ||
-      cfg->reserved2 != 0) {
-    set_error("%s: bad run config (schedule/precision/tally_mode/block/stack_depth)", who);
+      cfg->tally_atomics > 2) {
+    set_error("%s: bad run config (schedule/precision/tally_mode/block/stack_depth/tally_atomics)", who);
     return MC_ERR_ARG;
   }
   return MC_OK;
@@ -499,6 +500,7 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   L.num_sms = ctx->num_sms;
   L.pool_lock_attempts = ctx->limits.pool_lock_attempts;
   L.event_iterations = ctx->limits.event_iterations;
+  L.tally_agg = mci::tally_agg_of(cfg->tally_atomics, mci::kSlabAggDefault);
   *out = L;
   return MC_OK;
 }
@@ -600,6 +602,7 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
     P.stack_depth = cfg->stack_depth ? cfg->stack_depth : 256u;
     P.seeding = problems[0].seeding;
     P.max_generations = ctx->limits.pulse_generations;
+    P.tally_agg = mci::tally_agg_of(cfg->tally_atomics, mci::kPulseAggDefault);
     if (problems[0].seeding != MC_SEED_STRIDE) {
       // overflow bank of 2^20 secondaries (32 MiB per generation bank)
       P.ovf_cap = 1ull << 20;

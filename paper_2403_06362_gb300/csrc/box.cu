@@ -82,7 +82,7 @@ __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64
   return lo;
 }
 
-template <int M, typename T>
+template <int M, typename T, bool AGG>
 __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
   __shared__ mcd::Affine tab[64];
   // A single problem's record is read on every flight: keep it in shared memory.
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
     } else {
       ++events;
       ++lc.flights;
-      const int o = mcb::box_flight<M, T>(*P, r, l, q, base, planes);
+      const int o = mcb::box_flight<M, T>(*P, r, l, q, base, planes, AGG);
       if (o == mcb::kBoxLeak) {
         ++lc.leaks;
         end = true;
@@ -220,9 +220,9 @@ __global__ void __launch_bounds__(256, 3) box_history_kernel(const BoxArgs a) {
 
 namespace {
 
-template <int M, typename T>
+template <int M, typename T, bool AGG>
 int launch_box_gen(const BoxArgs& a, int block, int bps, int num_sms, cudaStream_t s) {
-  auto k = box_history_kernel<M, T>;
+  auto k = box_history_kernel<M, T, AGG>;
   int per_sm = bps;
   if (per_sm <= 0) {
     int st = mci::cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, 0),
@@ -264,7 +264,7 @@ int run_box_history(const mci::BoxLaunch& L, cudaStream_t s) {
     a.total = n;
     a.child_out = bank[0];
     a.child_out_count = cnt[0];
-    int st = launch_box_gen<M, T>(a, L.block, L.blocks_per_sm, L.num_sms, s);
+    int st = (L.tally_agg ? launch_box_gen<M, T, true> : launch_box_gen<M, T, false>)(a, L.block, L.blocks_per_sm, L.num_sms, s);
     if (st != MC_OK) return st;
     int cur = 0;
     for (int gen = 1;; ++gen) {
@@ -290,7 +290,7 @@ int run_box_history(const mci::BoxLaunch& L, cudaStream_t s) {
       a.total = made;
       a.child_out = bank[nxt];
       a.child_out_count = cnt[nxt];
-      st = launch_box_gen<M, T>(a, L.block, L.blocks_per_sm, L.num_sms, s);
+      st = (L.tally_agg ? launch_box_gen<M, T, true> : launch_box_gen<M, T, false>)(a, L.block, L.blocks_per_sm, L.num_sms, s);
       if (st != MC_OK) return st;
       cur = nxt;
     }

@@ -203,7 +203,8 @@ template <> __device__ __forceinline__ int voxel_guess<float>(const BoxDev& b, f
 // t = (plane - p) / u, so every piece has the length the clipping definition
 // gives it.  base: this history's [mesh^3] slot row.
 template <typename T>
-__device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long* base, const double* tab) {
+__device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long* base, const double* tab,
+                      bool agg) {
   const int nm = (int)b.mesh;
   const T h = sel<T>(b.h, b.h_f), inv_h = sel<T>(b.inv_h, b.inv_h_f);
   int idx[3];
@@ -233,7 +234,8 @@ __device__ void trace(const BoxDev& b, const Part<T>& q, T L, unsigned long long
       const long long v = fix_of(w * (tend - t));
       if (v != 0) {
         const uint64_t slot = ((uint64_t)idx[2] * nm + idx[1]) * nm + idx[0];
-        atomicAdd(base + slot, (unsigned long long)v);
+        if (agg) mcd::warp_agg_add(base + slot, (unsigned long long)v);
+        else atomicAdd(base + slot, (unsigned long long)v);
       }
       t = tend;
     }
@@ -266,7 +268,7 @@ __device__ __forceinline__ void box_source(const BoxDev& b, mcs::Rng<M>& r, cons
 // region (moved to the surface), or leak out of the box.
 template <int M, typename T>
 __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const mcd::Lcg& l, Part<T>& q,
-                                          unsigned long long* base, const double* tab = nullptr) {
+                                          unsigned long long* base, const double* tab, bool agg) {
   int kind = 0;
   T ds = surface<T>(b, q, kind);
   bool collide;
@@ -294,7 +296,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
     }
   }
   const T len = collide ? d : ds;
-  trace<T>(b, q, len, base, tab);
+  trace<T>(b, q, len, base, tab, agg);
   for (int a = 0; a < 3; ++a) q.p[a] = q.p[a] + len * q.u[a];
   if (collide) return kBoxCollide;
   if (kind == 2) return kBoxLeak;

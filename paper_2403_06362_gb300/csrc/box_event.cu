@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) flight_kernel(Args a) {
     b.events[s] = ev + 1;
     mcb::Part<T> q;
     load_part<T>(b, s, q);
-    const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, a.tally + b.tbase[s]);
+    const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, a.tally + b.tbase[s], nullptr, false);
     if (o == mcb::kBoxLeak) {
       finish(a, s, o, r.x, r.draws, ec);
       continue;
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(256) tail_kernel(Args a) {
     for (;;) {
       if (ev == a.event_cap) { outcome = -1; break; }
       ++ev;
-      const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, base);
+      const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, base, nullptr, false);
       if (o == mcb::kBoxLeak) { outcome = o; break; }
       if (o != mcb::kBoxCollide) continue;  // crossed into the other region
       ++co;

@@ -60,6 +60,18 @@ inline mc_limits default_limits() {
   return l;
 }
 
+// Warp-aggregated tally atomics for a run: mc_run_config.tally_atomics 1
+// (per lane) or 2 (aggregated), else the kernel's default.
+inline bool tally_agg_of(uint32_t tally_atomics, bool kernel_default) {
+  return tally_atomics == 0 ? kernel_default : tally_atomics == 2;
+}
+// Defaults (measured): one atomic per lane in every kernel.  The atomics are
+// not the bound of any of them, so the grouping (a match, three reductions
+// and a branch per contribution) costs more issue slots than it saves.
+constexpr bool kSlabAggDefault = false;
+constexpr bool kBoxAggDefault = false;
+constexpr bool kPulseAggDefault = false;
+
 // Instantiated launch graphs of the history schedule, keyed by launch shape.
 struct GraphCache {
   std::unordered_map<uint64_t, cudaGraphExec_t> m;

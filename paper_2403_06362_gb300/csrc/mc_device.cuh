@@ -205,6 +205,30 @@ __device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
   }
   return v;
 }
+// Warp-aggregated int64 tally add.  The lanes that arrive here together
+// (__activemask) and add to the same address form one group
+// (__match_any_sync); the group's values are summed and its lowest lane
+// issues the one atomic.  The sum runs on three 32-bit reductions of 26-,
+// 26- and 12-bit pieces of each value: 32 pieces of at most 26 bits sum
+// below 2^31, so every partial is exact and the recombined total equals
+// the 64-bit sum mod 2^64, the same value the group's separate atomics
+// would have added.  Integer addition is associative, so the tally bits do
+// not depend on how the lanes happened to group.
+__device__ __forceinline__ void warp_agg_add(unsigned long long* p, unsigned long long v) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, reinterpret_cast<unsigned long long>(p));
+  const unsigned lane = threadIdx.x & 31u;
+  if (peers == (1u << lane)) {  // alone on this address: no reduction
+    atomicAdd(p, v);
+    return;
+  }
+  const unsigned s0 = __reduce_add_sync(peers, (unsigned)v & 0x3ffffffu);
+  const unsigned s1 = __reduce_add_sync(peers, (unsigned)(v >> 26) & 0x3ffffffu);
+  const unsigned s2 = __reduce_add_sync(peers, (unsigned)(v >> 52));
+  if (lane == (unsigned)(__ffs(peers) - 1))
+    atomicAdd(p, (unsigned long long)s0 + ((unsigned long long)s1 << 26) + ((unsigned long long)s2 << 52));
+}
+
 // The problem index all lanes with counts share: -1 when no lane has counts,
 // -2 when lanes hold counts of different problems.
 __device__ __forceinline__ int warp_common_prob(int prob) {

@@ -170,5 +170,6 @@ extern "C" MC_API int mc_transport_run_static(const mc_lcg* lcg, const mc_proble
   L.block = cfg->block ? (int)cfg->block : mci::slab_default_block(L.total, L.chunk, slot->num_sms);
   L.blocks_per_sm = (int)cfg->blocks_per_sm;
   L.num_sms = slot->num_sms;
+  L.tally_agg = mci::tally_agg_of(cfg->tally_atomics, mci::kSlabAggDefault);
   return mci::slab_history_launch(L, s);
 }

@@ -108,7 +108,7 @@ struct PulseCounts {
   }
 };
 
-template <int M, bool HASH>
+template <int M, bool HASH, bool AGG>
 __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
   __shared__ mcd::Affine tab[64];
   __shared__ PulseDev sP;
@@ -204,7 +204,8 @@ __global__ void __launch_bounds__(256) pulse_kernel(const PulseArgs a) {
         if (mcx::abs_le(xn, P.x_half)) {
           const uint64_t jf = mcx::floor_nonneg(tn);
           const uint32_t j = jf < P.n_time_bins ? (uint32_t)jf : P.n_time_bins - 1;
-          atomicAdd(row + j, (unsigned long long)P.unit);
+          if constexpr (AGG) mcd::warp_agg_add(row + j, (unsigned long long)P.unit);
+          else atomicAdd(row + j, (unsigned long long)P.unit);
         }
         x = xn;
         t = tn;
@@ -316,11 +317,18 @@ int pulse_prep(void* d_prob, cudaStream_t s) {
   return cuda_status(cudaGetLastError(), "pulse_prep_kernel launch");
 }
 
+// The kernel variant for the LCG width, the seeding mode and the tally atomics.
+static void (*pulse_kernel_for(uint32_t m, bool hash, bool agg))(const PulseArgs) {
+  if (agg) return m == 63 ? (hash ? pulse_kernel<63, true, true> : pulse_kernel<63, false, true>)
+                          : (hash ? pulse_kernel<0, true, true> : pulse_kernel<0, false, true>);
+  return m == 63 ? (hash ? pulse_kernel<63, true, false> : pulse_kernel<63, false, false>)
+                 : (hash ? pulse_kernel<0, true, false> : pulse_kernel<0, false, false>);
+}
+
 // The largest grid pulse_run launches for L (one persistent block per slot).
 static int pulse_full_grid(const PulseLaunch& L, uint64_t* full_out) {
   const bool hash = L.seeding != MC_SEED_STRIDE;
-  auto k = L.lcg.m == 63 ? (hash ? pulse_kernel<63, true> : pulse_kernel<63, false>)
-                         : (hash ? pulse_kernel<0, true> : pulse_kernel<0, false>);
+  auto k = pulse_kernel_for(L.lcg.m, hash, L.tally_agg);
   int per_sm = 0;
   int st = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, L.block, 0),
                        "cudaOccupancyMaxActiveBlocksPerMultiprocessor(pulse)");
@@ -354,8 +362,7 @@ int pulse_run(const PulseLaunch& L, cudaStream_t s) {
   a.stack_depth = L.stack_depth;
   a.stack = static_cast<mcp::StackRec*>(L.d_stack);
   const bool hash = L.seeding != MC_SEED_STRIDE;
-  auto k = L.lcg.m == 63 ? (hash ? pulse_kernel<63, true> : pulse_kernel<63, false>)
-                         : (hash ? pulse_kernel<0, true> : pulse_kernel<0, false>);
+  auto k = pulse_kernel_for(L.lcg.m, hash, L.tally_agg);
   uint64_t full = 0;
   int st = pulse_full_grid(L, &full);
   if (st != MC_OK) return st;

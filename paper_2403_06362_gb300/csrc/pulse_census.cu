@@ -145,7 +145,7 @@ struct StagedItem {
   GroupCtl gc;
 };
 
-template <int M>
+template <int M, bool AGG>
 __global__ void __maxnreg__(96) pulse_census_kernel(const CensusArgs a) {
   extern __shared__ StagedItem s_items[];
   __shared__ PulseDev sP;
@@ -316,7 +316,8 @@ __global__ void __maxnreg__(96) pulse_census_kernel(const CensusArgs a) {
         if (mcx::abs_le(xn, P.x_half)) {
           const uint64_t jf = mcx::floor_nonneg(tn);
           const uint32_t j = jf < P.n_time_bins ? (uint32_t)jf : P.n_time_bins - 1;
-          atomicAdd(row + j, (unsigned long long)unit_w);
+          if constexpr (AGG) mcd::warp_agg_add(row + j, (unsigned long long)unit_w);
+          else atomicAdd(row + j, (unsigned long long)unit_w);
         }
         x = xn;
         t = tn;
@@ -431,7 +432,8 @@ int pulse_census_run(const PulseCensusLaunch& L, cudaStream_t s) {
   off += align256(L.groups * sizeof(GroupCtl));
   BankRec* bank[2] = {reinterpret_cast<BankRec*>(base + off),
                       reinterpret_cast<BankRec*>(base + off + align256(L.cap * sizeof(BankRec)))};
-  auto k = L.base.lcg.m == 63 ? pulse_census_kernel<63> : pulse_census_kernel<0>;
+  auto k = L.base.tally_agg ? (L.base.lcg.m == 63 ? pulse_census_kernel<63, true> : pulse_census_kernel<0, true>)
+                            : (L.base.lcg.m == 63 ? pulse_census_kernel<63, false> : pulse_census_kernel<0, false>);
   const int stage = L.base.chunk <= kPrefetch ? 1 : 0;
   const size_t stage_smem = stage ? (size_t)(L.base.block / 32) * L.base.chunk * sizeof(StagedItem) : 0u;
   int per_sm = 0;

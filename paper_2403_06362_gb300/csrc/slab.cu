@@ -155,7 +155,7 @@ __device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, u
   return lo;
 }
 
-template <int M, bool F32, bool SMEM>
+template <int M, bool F32, bool SMEM, bool AGG>
 __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   extern __shared__ unsigned long long s_tally[];
   __shared__ mcd::Affine tab[64];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   const SlabDev* P = a.probs;
   mcs::Rng<M> r{0ull, 0ull};
   mcs::SlabParticle q{};
-  mcs::Sink sink{nullptr, s_edges, s_widths};
+  mcs::Sink sink{nullptr, s_edges, s_widths, AGG};
   uint64_t gi = 0, events = 0;
 
   for (;;) {
@@ -354,9 +354,9 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   }
 }
 
-template <int M, bool F32, bool SMEM>
+template <int M, bool F32, bool SMEM, bool AGG>
 int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
-  auto k = slab_history_kernel<M, F32, SMEM>;
+  auto k = slab_history_kernel<M, F32, SMEM, AGG>;
   RunArgs a = a0;
   // Static shared memory of this instantiation (read once) and the device's
   // opt-in limit: what does not fit beside them is given up, the compaction
@@ -403,13 +403,13 @@ int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms,
   return mci::cuda_status(cudaGetLastError(), "slab_history_kernel launch");
 }
 
-template <int M>
+template <int M, bool AGG>
 int launch_history_m(const RunArgs& a, bool f32, int block, int bps, int sms, cudaStream_t s) {
   const bool smem = a.smem_slots != 0;
-  if (f32) return smem ? launch_history<M, true, true>(a, block, bps, sms, s)
-                       : launch_history<M, true, false>(a, block, bps, sms, s);
-  return smem ? launch_history<M, false, true>(a, block, bps, sms, s)
-              : launch_history<M, false, false>(a, block, bps, sms, s);
+  if (f32) return smem ? launch_history<M, true, true, AGG>(a, block, bps, sms, s)
+                       : launch_history<M, true, false, AGG>(a, block, bps, sms, s);
+  return smem ? launch_history<M, false, true, AGG>(a, block, bps, sms, s)
+              : launch_history<M, false, false, AGG>(a, block, bps, sms, s);
 }
 
 }  // namespace
@@ -486,8 +486,12 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
   a.donate_max = 12;
   a.pool_cap = L.block >= 64 ? (uint32_t)((L.block >> 5) - 1) * a.donate_max : 0u;
   a.lock_attempts = L.pool_lock_attempts;
-  if (L.lcg.m == 63) return launch_history_m<63>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
-  return launch_history_m<0>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+  if (L.tally_agg) {
+    if (L.lcg.m == 63) return launch_history_m<63, true>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+    return launch_history_m<0, true>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+  }
+  if (L.lcg.m == 63) return launch_history_m<63, false>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
+  return launch_history_m<0, false>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
 }
 
 }  // namespace mci

@@ -107,8 +107,11 @@ struct Sink {
   unsigned long long* base;  // this history's [bin] row (smem or global)
   const double* edges;
   const double* widths;  // with edges: widths[j] = e_{j+1} - e_j (the same fp64 difference)
+  bool agg;              // warp-aggregated atomics (mcd::warp_agg_add) instead of one per lane
   __device__ __forceinline__ void add(int j, long long v) const {
-    if (v != 0) atomicAdd(base + j, (unsigned long long)v);
+    if (v == 0) return;
+    if (agg) mcd::warp_agg_add(base + j, (unsigned long long)v);
+    else atomicAdd(base + j, (unsigned long long)v);
   }
 };
 

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) ev_flight_kernel(EvArgs a) {
     } else {
       q.x = b.x[slot]; q.mu = b.mu[slot]; q.w_mu = b.w[slot];
     }
-    const mcs::Sink sink{a.tally + b.tbase[slot], nullptr, nullptr};
+    const mcs::Sink sink{a.tally + b.tbase[slot], nullptr, nullptr, false};
     const int o = mcs::slab_flight<M, F32>(P, r, a.lcg, q, sink);
     if (o != mcs::kCollide) {
       ev_finish(a, slot, o, r.x, r.draws, ec);
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(256) ev_tail_kernel(EvArgs a) {
     } else {
       q.x = b.x[slot]; q.mu = b.mu[slot]; q.w_mu = b.w[slot];
     }
-    const mcs::Sink sink{a.tally + b.tbase[slot], nullptr, nullptr};
+    const mcs::Sink sink{a.tally + b.tbase[slot], nullptr, nullptr, false};
     int outcome;
     for (;;) {
       if (ev == a.event_cap) { outcome = -1; break; }

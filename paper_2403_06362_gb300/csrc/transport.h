@@ -25,6 +25,7 @@ struct SlabLaunch {
   bool f32;
   int block, blocks_per_sm, num_sms;
   uint32_t pool_lock_attempts = 1u << 20;  // compaction-pool lock (mc_limits)
+  bool tally_agg = true;                   // warp-aggregated tally atomics
   uint64_t event_iterations = ~0ull;       // event schedule bound (mc_limits; ~0: derived)
 };
 
@@ -71,6 +72,7 @@ struct BoxLaunch {
   unsigned int* h_done;
   cudaStream_t capture_stream;
   uint32_t max_generations = 10000u;  // child generations (mc_limits)
+  bool tally_agg = true;              // warp-aggregated mesh atomics
   uint64_t event_iterations = ~0ull;  // per generation (mc_limits; ~0: derived)
 };
 
@@ -95,6 +97,7 @@ struct PulseLaunch {
   uint64_t ovf_cap;
   unsigned long long* h_count;
   uint32_t max_generations = 100000u;  // overflow generations (mc_limits)
+  bool tally_agg = true;               // warp-aggregated tally atomics
 };
 size_t pulse_ovf_bytes(uint64_t cap);
 
