@@ -239,6 +239,8 @@ def main():
                              "batched_fp32", "batched_fp64", "pulse_hash", "pulse_stride", "pulse_census"],
                     help="run one transport workload (a warm-up run, then one run) and exit; for profilers")
     ap.add_argument("--histories", type=int, default=0, help="history count for --profile-workload")
+    ap.add_argument("--schedule", type=int, default=0, choices=[0, 1],
+                    help="mc_run_config.schedule for --profile-workload (0 history, 1 event, as a captured graph)")
     ap.add_argument("--tally-atomics", type=int, default=0, choices=[0, 1, 2],
                     help="mc_run_config.tally_atomics for --profile-workload (0 library default, 1 per lane, "
                          "2 warp-aggregated)")
@@ -439,7 +441,8 @@ def profile_workload(args):
         cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
         tally = mc.Tally(W.tally_slots(probs), len(probs))
         n = sum(p["n_histories"] for p in probs)
-    cfg = mc.mc_run_config(precision=1 if "fp32" in name else 0, tally_atomics=args.tally_atomics)
+    cfg = mc.mc_run_config(precision=1 if "fp32" in name else 0, tally_atomics=args.tally_atomics,
+                           schedule=args.schedule, use_graph=args.schedule)
     times = []
     for _ in range(2):
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -1,12 +1,27 @@
 // box_event.cu -- event-based schedule of the two-region box.
 //
-// Same structure as the slab event schedule: particles in a device bank,
-// one kernel per event type over queues of bank slots (plan, refill,
-// flight, collide, advance), iterations launched in batches by the host
-// (optionally as a captured graph).  Split children go to a device child
-// bank and are followed as the next generation, exactly as in the history
-// schedule.  All per-particle arithmetic is box.cuh's, so the int64 mesh
-// tally is bit-identical to the history schedule's.
+// Particles live in device banks instead of registers, one array per field
+// (structure of arrays).  Each iteration is ONE kernel that streams the
+// current bank in slot order -- every field load of a warp is one coalesced
+// access -- and moves each particle one event: it flies, and if it stops at
+// a collision site it collides.  Survivors are appended to the other bank
+// (one atomic per group of converged lanes, so a group's stores land in
+// consecutive slots), which keeps the bank dense: no dead slots, no queue.
+// A particle that ended (leak, roulette, event cap) is replaced in the same
+// pass by the next item of the generation from a ticket (a source history
+// or a split child), so the bank stays full while there is work.  The block
+// that finishes last (a counter, no waiting) swaps the banks and sets the
+// completion flag.  The host launches iterations in batches (optionally one
+// captured graph per batch) and reads the flag between batches; no kernel
+// waits on another.
+//
+// Split children go to a device child bank and are followed as the next
+// generation, exactly as in the history schedule.  Once every item of a
+// generation has started and the live particles no longer fill the GPU, one
+// tail kernel runs each live particle to its end.  All per-particle
+// arithmetic is box.cuh's (the same draws, in the same order, and the same
+// int64 contributions), so the mesh tally is bit-identical to the history
+// schedule's.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,25 +37,38 @@ using mcb::BoxDev;
 using mcb::ChildRec;
 
 struct Ctl {
-  unsigned int nfq[2], ncq, nfree, cur, refill_n, refill_free_base, done;
-  unsigned long long refill_ticket_base, ticket, iters;
+  unsigned int n[2];           // particles in each bank
+  unsigned int cur;            // the bank the next iteration reads
+  unsigned int done;           // 1: generation finished; 2: tail kernel next
+  unsigned int blocks_done;    // blocks of the running iteration that finished
+  unsigned int pad;
+  unsigned long long ticket;   // next item of the generation
+  unsigned long long iters;
 };
 
+// One bank: an array per field.  T = float: 92 bytes per particle;
+// T = double: 132.
+template <typename T>
+struct SoA {
+  T *p[3], *u[3], *inv[3], *w;
+  uint64_t *rng, *draws, *events, *gi, *tbase;
+  uint32_t *prob, *flags;  // flags: group | region << 8 | primary << 16
+};
+
+template <typename T>
 struct Bank {
   Ctl* ctl;
-  mcd::Affine* tab;
-  double *px, *py, *pz, *ux, *uy, *uz, *w;
-  uint64_t *rng, *draws, *events, *gi, *tbase;
-  uint32_t *prob, *grp, *region, *primary, *coll;
-  uint32_t *fq0, *fq1, *cq, *freeq;
+  mcd::Affine* tab;  // maps of 2^j LCG steps (stride seeding)
+  SoA<T> f[2];
   uint32_t cap;
 };
 
+template <typename T>
 struct Args {
-  uint32_t tail_threshold;  // live particles at or below which the tail kernel takes over
+  uint32_t tail_threshold;   // live particles at or below which the tail kernel takes over
   const BoxDev* probs;
   uint32_t nprob;
-  const ChildRec* child_in;  // nullptr: source histories
+  const ChildRec* child_in;  // nullptr: the items are source histories
   uint64_t range_begin, total;
   ChildRec* child_out;
   unsigned long long* child_out_count;
@@ -51,12 +79,13 @@ struct Args {
   uint64_t* hist_draws;
   mcd::Lcg lcg;
   uint64_t event_cap;
-  Bank b;
+  Bank<T> b;
 };
 
 size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
-size_t carve(void* base, uint32_t cap, Bank* out) {
+template <typename T>
+size_t carve(void* base, uint32_t cap, Bank<T>* out) {
   char* p = static_cast<char*>(base);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -64,21 +93,77 @@ size_t carve(void* base, uint32_t cap, Bank* out) {
     off += a256(bytes);
     return q;
   };
-  Bank b{};
+  Bank<T> b{};
   b.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
   b.tab = reinterpret_cast<mcd::Affine*>(take(64 * sizeof(mcd::Affine)));
-  double** dd[] = {&b.px, &b.py, &b.pz, &b.ux, &b.uy, &b.uz, &b.w};
-  for (double** d : dd) *d = reinterpret_cast<double*>(take((size_t)cap * 8));
-  uint64_t** uu[] = {&b.rng, &b.draws, &b.events, &b.gi, &b.tbase};
-  for (uint64_t** u : uu) *u = reinterpret_cast<uint64_t*>(take((size_t)cap * 8));
-  uint32_t** ii[] = {&b.prob, &b.grp, &b.region, &b.primary, &b.coll, &b.fq0, &b.fq1, &b.cq, &b.freeq};
-  for (uint32_t** i : ii) *i = reinterpret_cast<uint32_t*>(take((size_t)cap * 4));
+  for (int k = 0; k < 2; ++k) {
+    SoA<T>& f = b.f[k];
+    for (int a = 0; a < 3; ++a) {
+      f.p[a] = reinterpret_cast<T*>(take((size_t)cap * sizeof(T)));
+      f.u[a] = reinterpret_cast<T*>(take((size_t)cap * sizeof(T)));
+      f.inv[a] = reinterpret_cast<T*>(take((size_t)cap * sizeof(T)));
+    }
+    f.w = reinterpret_cast<T*>(take((size_t)cap * sizeof(T)));
+    uint64_t** uu[] = {&f.rng, &f.draws, &f.events, &f.gi, &f.tbase};
+    for (uint64_t** x : uu) *x = reinterpret_cast<uint64_t*>(take((size_t)cap * 8));
+    f.prob = reinterpret_cast<uint32_t*>(take((size_t)cap * 4));
+    f.flags = reinterpret_cast<uint32_t*>(take((size_t)cap * 4));
+  }
   b.cap = cap;
   if (out) *out = b;
   return off;
 }
 
-__device__ __forceinline__ void warp_append(unsigned int* counter, uint32_t* q, uint32_t slot) {
+// A particle as the kernels hold it.
+template <typename T>
+struct Live {
+  mcb::Part<T> q;
+  uint64_t rng, draws, events, gi, tbase;
+  uint32_t prob, primary;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_live(const SoA<T>& f, uint32_t s, Live<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    v.q.p[a] = f.p[a][s];
+    v.q.u[a] = f.u[a][s];
+    v.q.inv[a] = f.inv[a][s];
+  }
+  v.q.w = f.w[s];
+  v.rng = f.rng[s];
+  v.draws = f.draws[s];
+  v.events = f.events[s];
+  v.gi = f.gi[s];
+  v.tbase = f.tbase[s];
+  v.prob = f.prob[s];
+  const uint32_t fl = f.flags[s];
+  v.q.g = fl & 0xffu;
+  v.q.region = (fl >> 8) & 0xffu;
+  v.primary = fl >> 16;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_live(const SoA<T>& f, uint32_t s, const Live<T>& v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f.p[a][s] = v.q.p[a];
+    f.u[a][s] = v.q.u[a];
+    f.inv[a][s] = v.q.inv[a];
+  }
+  f.w[s] = v.q.w;
+  f.rng[s] = v.rng;
+  f.draws[s] = v.draws;
+  f.events[s] = v.events;
+  f.gi[s] = v.gi;
+  f.tbase[s] = v.tbase;
+  f.prob[s] = v.prob;
+  f.flags[s] = v.q.g | (v.q.region << 8) | (v.primary << 16);
+}
+
+// A slot in a bank for each converged lane that asks (one atomic per
+// group: the group's slots are consecutive).
+__device__ __forceinline__ uint32_t take_slot(unsigned int* counter) {
   const unsigned mask = __activemask();
   const int leader = __ffs(mask) - 1;
   const unsigned lane = threadIdx.x & 31u;
@@ -86,55 +171,20 @@ __device__ __forceinline__ void warp_append(unsigned int* counter, uint32_t* q, 
   unsigned base = 0;
   if ((int)lane == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
   base = __shfl_sync(mask, base, leader);
-  q[base + rank] = slot;
+  return base + rank;
 }
 
-template <typename T>
-__device__ __forceinline__ void load_part(const Bank& b, uint32_t s, mcb::Part<T>& q) {
-  q.p[0] = (T)b.px[s]; q.p[1] = (T)b.py[s]; q.p[2] = (T)b.pz[s];
-  q.u[0] = (T)b.ux[s]; q.u[1] = (T)b.uy[s]; q.u[2] = (T)b.uz[s];
-  q.w = (T)b.w[s];
-  q.g = b.grp[s];
-  q.region = b.region[s];
-  mcb::set_inv(q);
-}
-
-template <typename T>
-__device__ __forceinline__ void store_part(const Bank& b, uint32_t s, const mcb::Part<T>& q) {
-  b.px[s] = (double)q.p[0]; b.py[s] = (double)q.p[1]; b.pz[s] = (double)q.p[2];
-  b.ux[s] = (double)q.u[0]; b.uy[s] = (double)q.u[1]; b.uz[s] = (double)q.u[2];
-  b.w[s] = (double)q.w;
-  b.grp[s] = q.g;
-  b.region[s] = q.region;
-}
-
-__global__ void init_kernel(Args a) {
-  const Bank& b = a.b;
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = tid; i < b.cap; i += nt) b.freeq[i] = (uint32_t)(b.cap - 1 - i);
-  if (tid == 0) {
-    Ctl* c = b.ctl;
-    c->nfq[0] = c->nfq[1] = 0;
-    c->ncq = 0;
-    c->nfree = b.cap;
-    c->cur = 0;
-    c->refill_n = c->refill_free_base = 0;
-    c->done = a.total == 0 ? 1u : 0u;
-    c->refill_ticket_base = c->ticket = c->iters = 0;
-    mcd::Affine sq{a.lcg.g, a.lcg.c};
-    for (int j = 0; j < 64; ++j) { b.tab[j] = sq; sq = mcd::compose(sq, sq); }
-  }
-}
-
-__global__ void plan_kernel(Args a) {
-  Ctl* c = a.b.ctl;
-  const uint64_t F = c->nfree, R = a.total - c->ticket;
-  const uint64_t n = F < R ? F : R;
-  c->refill_n = (unsigned int)n;
-  c->refill_free_base = (unsigned int)(F - n);
-  c->refill_ticket_base = c->ticket;
-  c->nfree = (unsigned int)(F - n);
-  c->ticket += n;
+// The next item of the generation for each converged lane that asks (one
+// atomic per group); a value >= total once the ticket has run out.
+__device__ __forceinline__ unsigned long long take_item(unsigned long long* ticket) {
+  const unsigned mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+  unsigned long long base = 0;
+  if ((int)lane == leader) base = atomicAdd(ticket, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + rank;
 }
 
 __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64_t gi) {
@@ -146,228 +196,251 @@ __device__ __forceinline__ uint32_t find_box(const BoxDev* p, uint32_t n, uint64
   return lo;
 }
 
+// Starts item `item` of the generation in `v` (a source history: its seed
+// and source sample; a child: its record from the child bank).
 template <int M, typename T>
-__global__ void __launch_bounds__(256) refill_kernel(Args a) {
-  const Bank& b = a.b;
-  const Ctl* c = b.ctl;
-  const uint32_t n = c->refill_n, fb = c->refill_free_base;
-  const uint64_t tb = c->refill_ticket_base;
-  uint32_t* fq = c->cur ? b.fq1 : b.fq0;
-  unsigned int* nfq = &b.ctl->nfq[c->cur];
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = tid; t < n; t += nt) {
-    const uint32_t s = b.freeq[fb + t];
-    const uint64_t item = tb + t;
-    mcb::Part<T> q{};
-    mcs::Rng<M> r{0ull, 0ull};
-    uint32_t pi;
-    if (a.child_in == nullptr) {
-      const uint64_t gi = a.range_begin + item;
-      pi = a.nprob == 1 ? 0u : find_box(a.probs, a.nprob, gi);
-      const BoxDev& P = a.probs[pi];
-      const uint64_t id = gi - P.hist_begin;
-      const uint64_t nvox = (uint64_t)P.mesh * P.mesh * P.mesh;
-      const uint64_t seed = P.seeding == MC_SEED_STRIDE
-                                ? mcs::skip_tab(b.tab, P.seed, P.stride_q * (P.id_offset + id)) & a.lcg.mask
-                                : mcd::hash_with(id, P.seed_hash) & a.lcg.mask;
-      r = mcs::Rng<M>{seed, 0ull};
-      mcb::box_source<M, T>(P, r, a.lcg, q);
-      b.gi[s] = gi;
-      b.tbase[s] = P.tally_offset + mcs::batch_of(id, P.n_hist, P.n_batches) * nvox;
-      b.primary[s] = 1u;
-    } else {
-      const ChildRec cr = a.child_in[item];
-      pi = cr.prob;
-      r = mcs::Rng<M>{cr.rng, 0ull};
-      mcb::load_child<T>(cr, q);
-      b.gi[s] = 0;
-      b.tbase[s] = cr.tbase;
-      b.primary[s] = 0u;
-    }
-    b.prob[s] = pi;
-    b.rng[s] = r.x;
-    b.draws[s] = r.draws;
-    b.events[s] = 0;
-    b.coll[s] = 0;
-    store_part<T>(b, s, q);
-    warp_append(nfq, fq, s);
+__device__ __forceinline__ void start_item(const Args<T>& a, const mcd::Affine* tab, uint64_t item, Live<T>& v) {
+  mcs::Rng<M> r{0ull, 0ull};
+  v.q = mcb::Part<T>{};
+  if (a.child_in == nullptr) {
+    const uint64_t gi = a.range_begin + item;
+    const uint32_t pi = a.nprob == 1 ? 0u : find_box(a.probs, a.nprob, gi);
+    const BoxDev& P = a.probs[pi];
+    const uint64_t id = gi - P.hist_begin;
+    const uint64_t nvox = (uint64_t)P.mesh * P.mesh * P.mesh;
+    const uint64_t seed = P.seeding == MC_SEED_STRIDE
+                              ? mcs::skip_tab(tab, P.seed, P.stride_q * (P.id_offset + id)) & a.lcg.mask
+                              : mcd::hash_with(id, P.seed_hash) & a.lcg.mask;
+    r = mcs::Rng<M>{seed, 0ull};
+    mcb::box_source<M, T>(P, r, a.lcg, v.q);
+    v.gi = gi;
+    v.tbase = P.tally_offset + mcs::batch_of(id, P.n_hist, P.n_batches) * nvox;
+    v.prob = pi;
+    v.primary = 1u;
+  } else {
+    const ChildRec cr = a.child_in[item];
+    r = mcs::Rng<M>{cr.rng, 0ull};
+    mcb::load_child<T>(cr, v.q);
+    v.gi = 0;
+    v.tbase = cr.tbase;
+    v.prob = cr.prob;
+    v.primary = 0u;
   }
+  v.rng = r.x;
+  v.draws = r.draws;
+  v.events = 0;
 }
 
-// outcome: mcb::kBoxLeak, kBoxKilled, or -1 (event cap).  The particle's
-// counts go to the thread's counters `ec` (flushed by its warp at the end of
-// the kernel, or here when the problem changes).
-__device__ void finish(const Args& a, uint32_t s, int outcome, uint64_t rng_x, uint64_t draws, mcb::BoxCounts& ec) {
-  const Bank& b = a.b;
-  const uint32_t pi = b.prob[s];
-  const BoxDev& P = a.probs[pi];
-  if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
-  const bool prim = b.primary[s] != 0u;
+// The end of a particle: counters into the thread's `ec` (flushed by its
+// warp at the end of the kernel, or here when the problem changes) and the
+// per-history outputs of a source history.  outcome: kBoxLeak, kBoxKilled
+// or -1 (event cap).
+template <typename T>
+__device__ void finish(const Args<T>& a, const BoxDev& P, const Live<T>& v, int outcome, mcb::BoxCounts& ec) {
+  if ((int)v.prob != ec.prob) { ec.flush(a.counts); ec.prob = (int)v.prob; }
+  const bool prim = v.primary != 0u;
   if (prim) ++ec.src;
-  ec.flights += (uint32_t)b.events[s];
-  ec.coll += b.coll[s];
   if (outcome == mcb::kBoxLeak) ++ec.leaks;
   else if (outcome == mcb::kBoxKilled) ++ec.kills;
   else ++ec.capped;
-  ec.draws += draws;
-  if (draws > ec.maxd) ec.maxd = draws;
+  ec.draws += v.draws;
+  if (v.draws > ec.maxd) ec.maxd = v.draws;
   if (prim) {
-    if (P.stride_q != 0 && draws > P.stride_q) {
+    if (P.stride_q != 0 && v.draws > P.stride_q) {
       ++ec.exh;
-      ec.exd += draws - P.stride_q;
+      ec.exd += v.draws - P.stride_q;
     }
-    const uint64_t gi = b.gi[s];
-    if (a.hist_state) a.hist_state[gi] = rng_x & a.lcg.mask;
-    if (a.hist_draws) a.hist_draws[gi] = draws;
+    if (a.hist_state) a.hist_state[v.gi] = v.rng & a.lcg.mask;
+    if (a.hist_draws) a.hist_draws[v.gi] = v.draws;
   }
   if (ec.draws > (1ull << 31) || ec.flights > (1u << 30)) ec.flush(a.counts);
-  const unsigned int k = atomicAdd(&b.ctl->nfree, 1u);
-  b.freeq[k] = s;
 }
 
-template <int M, typename T>
-__global__ void __launch_bounds__(256) flight_kernel(Args a) {
-  const Bank& b = a.b;
-  const unsigned int cur = b.ctl->cur;
-  const uint32_t n = b.ctl->nfq[cur];
-  const uint32_t* fq = cur ? b.fq1 : b.fq0;
-  uint32_t* fnext = cur ? b.fq0 : b.fq1;
-  unsigned int* nnext = &b.ctl->nfq[cur ^ 1u];
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
-  mcb::BoxCounts ec;
-  ec.prob = -1;
-  ec.clear();
-  for (uint64_t t = tid; t < n; t += nt) {
-    const uint32_t s = fq[t];
-    const BoxDev& P = a.probs[b.prob[s]];
-    mcs::Rng<M> r{b.rng[s], b.draws[s]};
-    const uint64_t ev = b.events[s];
-    if (ev == a.event_cap) {
-      finish(a, s, -1, r.x, r.draws, ec);
-      continue;
-    }
-    b.events[s] = ev + 1;
-    mcb::Part<T> q;
-    load_part<T>(b, s, q);
-    const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, a.tally + b.tbase[s], nullptr, false);
-    if (o == mcb::kBoxLeak) {
-      finish(a, s, o, r.x, r.draws, ec);
-      continue;
-    }
-    b.rng[s] = r.x;
-    b.draws[s] = r.draws;
-    b.px[s] = (double)q.p[0]; b.py[s] = (double)q.p[1]; b.pz[s] = (double)q.p[2];
-    b.region[s] = q.region;
-    if (o == mcb::kBoxCollide) warp_append(&b.ctl->ncq, b.cq, s);
-    else warp_append(nnext, fnext, s);
+// Split children of the collision just made go to the next generation.
+template <typename T>
+__device__ __forceinline__ void bank_children(const Args<T>& a, int c, const mcb::Part<T>& q, uint64_t rng,
+                                              uint32_t prob, uint64_t tbase, mcb::BoxCounts& ec) {
+  const uint32_t ns = (uint32_t)(c - mcb::kSplitBase);
+  ++ec.splits;
+  ec.children += ns - 1;
+  for (uint32_t k = 0; k + 1 < ns; ++k) {
+    const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
+    if (idx < a.child_cap) mcb::store_child<T>(a.child_out[idx], q, mcb::child_seed(k, rng, a.lcg.mask), prob, tbase);
   }
-  ec.flush_warp(a.counts);
 }
 
+// Shared-memory copies of a single problem's record and (fp64) mesh planes,
+// read on every flight and voxel crossing.
+template <typename T>
+struct SharedProblem {
+  unsigned char prob[sizeof(BoxDev)];
+  double planes[sizeof(T) == 8 ? mcb::kMaxPlanes : 1];
+};
+
+template <typename T>
+__device__ __forceinline__ const BoxDev* stage_problem(const Args<T>& a, SharedProblem<T>& sp,
+                                                       const double** planes) {
+  *planes = nullptr;
+  if (a.nprob != 1) return a.probs;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(a.probs);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(sp.prob);
+  for (uint32_t i = threadIdx.x; i < sizeof(BoxDev) / 8; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  const BoxDev* p = reinterpret_cast<const BoxDev*>(sp.prob);
+  if constexpr (sizeof(T) == 8) {
+    for (uint32_t j = threadIdx.x; j <= p->mesh; j += blockDim.x) sp.planes[j] = mcb::plane_of(*p, (int)j);
+    __syncthreads();
+    *planes = sp.planes;
+  }
+  return p;
+}
+
+// First pass of a generation: the first min(cap, total) items into bank 0,
+// and the control block reset.
 template <int M, typename T>
-__global__ void __launch_bounds__(256) collide_kernel(Args a) {
-  const Bank& b = a.b;
-  const unsigned int nxt = b.ctl->cur ^ 1u;
-  const uint32_t n = b.ctl->ncq;
-  uint32_t* fq = nxt ? b.fq1 : b.fq0;
-  unsigned int* nfq = &b.ctl->nfq[nxt];
+__global__ void __launch_bounds__(256) init_kernel(Args<T> a) {
+  __shared__ mcd::Affine tab[64];
+  if (threadIdx.x == 0) {
+    mcd::Affine sq{a.lcg.g, a.lcg.c};
+    for (int j = 0; j < 64; ++j) { tab[j] = sq; sq = mcd::compose(sq, sq); }
+  }
+  __syncthreads();
+  const Bank<T>& b = a.b;
+  const uint64_t n = a.total < b.cap ? a.total : b.cap;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = tid; i < n; i += nt) {
+    Live<T> v;
+    start_item<M, T>(a, tab, i, v);
+    store_live<T>(b.f[0], (uint32_t)i, v);
+  }
+  if (tid == 0) {
+    Ctl* c = b.ctl;
+    c->n[0] = (unsigned int)n;
+    c->n[1] = 0;
+    c->cur = 0;
+    // a generation that starts with every item in the bank and no more live
+    // particles than the tail threshold goes straight to the tail kernel
+    c->done = n == 0 ? 1u : ((n == a.total && n <= a.tail_threshold) ? 2u : 0u);
+    c->blocks_done = 0;
+    c->pad = 0;
+    c->ticket = n;
+    c->iters = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 64) b.tab[threadIdx.x] = tab[threadIdx.x];
+}
+
+// One iteration: every particle of the current bank flies once and, at a
+// collision site, collides; survivors, and the items that replace ended
+// particles, go to the other bank.  The last block to finish advances the
+// control block.
+template <int M, typename T>
+__global__ void __launch_bounds__(256, 3) step_kernel(Args<T> a) {
+  __shared__ __align__(16) SharedProblem<T> sp;
+  const double* planes = nullptr;
+  const BoxDev* probs = stage_problem<T>(a, sp, &planes);
+  const Bank<T>& b = a.b;
+  Ctl* c = b.ctl;
+  const unsigned int cur = c->cur;
+  const uint32_t n = c->n[cur];
+  const SoA<T>& fin = b.f[cur];
+  const SoA<T>& fout = b.f[cur ^ 1u];
+  unsigned int* nout = &c->n[cur ^ 1u];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
   mcb::BoxCounts ec;
   ec.prob = -1;
   ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
-    const uint32_t s = b.cq[t];
-    const uint32_t pi = b.prob[s];
-    const BoxDev& P = a.probs[pi];
-    mcs::Rng<M> r{b.rng[s], b.draws[s]};
-    mcb::Part<T> q;
-    load_part<T>(b, s, q);
-    b.coll[s] += 1u;
-    const int o = mcb::box_collide<M, T>(P, r, a.lcg, q);
-    if (o == mcb::kBoxKilled) {
-      finish(a, s, o, r.x, r.draws, ec);
-      continue;
-    }
-    if (o >= mcb::kSplitBase + 2) {
-      const uint32_t ns = (uint32_t)(o - mcb::kSplitBase);
-      if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
-      ++ec.splits;
-      ec.children += ns - 1;
-      for (uint32_t k = 0; k + 1 < ns; ++k) {
-        const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
-        if (idx < a.child_cap)
-          mcb::store_child<T>(a.child_out[idx], q, mcb::child_seed(k, r.x, a.lcg.mask), pi, b.tbase[s]);
+    Live<T> v;
+    load_live<T>(fin, (uint32_t)t, v);
+    const BoxDev& P = probs[v.prob];
+    mcs::Rng<M> r{v.rng, v.draws};
+    int outcome = -2;  // -2: alive after this iteration
+    if (v.events == a.event_cap) {
+      outcome = -1;
+    } else {
+      ++v.events;
+      if ((int)v.prob != ec.prob) { ec.flush(a.counts); ec.prob = (int)v.prob; }
+      ++ec.flights;
+      const int o = mcb::box_flight<M, T>(P, r, a.lcg, v.q, a.tally + v.tbase, planes, false);
+      if (o == mcb::kBoxLeak) {
+        outcome = o;
+      } else if (o == mcb::kBoxCollide) {
+        ++ec.coll;
+        const int cc = mcb::box_collide<M, T>(P, r, a.lcg, v.q);
+        if (cc == mcb::kBoxKilled) outcome = cc;
+        else if (cc >= mcb::kSplitBase + 2) bank_children<T>(a, cc, v.q, r.x, v.prob, v.tbase, ec);
       }
     }
-    b.rng[s] = r.x;
-    b.draws[s] = r.draws;
-    store_part<T>(b, s, q);
-    warp_append(nfq, fq, s);
+    v.rng = r.x;
+    v.draws = r.draws;
+    bool keep = true;
+    if (outcome != -2) {
+      finish<T>(a, P, v, outcome, ec);
+      const unsigned long long item = take_item(&c->ticket);
+      if (item < a.total) start_item<M, T>(a, b.tab, item, v);
+      else keep = false;
+    }
+    if (keep) store_live<T>(fout, take_slot(nout), v);
   }
   ec.flush_warp(a.counts);
+  // The last block to finish advances: the other blocks' stores and slot
+  // counts are visible after their fence and counter increment.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&c->blocks_done, 1u);
+    if (prev == gridDim.x - 1u) {
+      __threadfence();
+      const unsigned int live = atomicAdd(nout, 0u);
+      const unsigned long long tk = atomicAdd(&c->ticket, 0ull);
+      c->n[cur] = 0u;
+      c->cur = cur ^ 1u;
+      c->blocks_done = 0u;
+      c->iters += 1;
+      c->done = tk < a.total ? 0u : (live == 0 ? 1u : (live <= a.tail_threshold ? 2u : 0u));
+      __threadfence();
+    }
+  }
 }
 
-__global__ void advance_kernel(Args a) {
-  Ctl* c = a.b.ctl;
-  const unsigned int cur = c->cur;
-  c->nfq[cur] = 0;
-  c->ncq = 0;
-  c->cur = cur ^ 1u;
-  const unsigned int live = c->nfq[cur ^ 1u];
-  // 1: finished; 2: every particle of the generation started and few enough
-  // live for the tail kernel
-  c->done = c->ticket < a.total ? 0u : (live == 0 ? 1u : (live <= a.tail_threshold ? 2u : 0u));
-  c->iters += 1;
-}
-
-// The tail of a generation: each live particle of the current flight queue
-// flies, crosses and collides to its end in one thread (split children go
-// to the child bank as in collide_kernel).
+// The tail of a generation: each particle of the current bank flies,
+// crosses and collides to its end in one thread.
 template <int M, typename T>
-__global__ void __launch_bounds__(256) tail_kernel(Args a) {
-  const Bank& b = a.b;
+__global__ void __launch_bounds__(256, 3) tail_kernel(Args<T> a) {
+  __shared__ __align__(16) SharedProblem<T> sp;
+  const double* planes = nullptr;
+  const BoxDev* probs = stage_problem<T>(a, sp, &planes);
+  const Bank<T>& b = a.b;
   const unsigned int cur = b.ctl->cur;
-  const uint32_t n = b.ctl->nfq[cur];
-  const uint32_t* fq = cur ? b.fq1 : b.fq0;
+  const uint32_t n = b.ctl->n[cur];
+  const SoA<T>& fin = b.f[cur];
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (uint64_t)gridDim.x * blockDim.x;
   mcb::BoxCounts ec;
   ec.prob = -1;
   ec.clear();
   for (uint64_t t = tid; t < n; t += nt) {
-    const uint32_t s = fq[t];
-    const uint32_t pi = b.prob[s];
-    const BoxDev& P = a.probs[pi];
-    mcs::Rng<M> r{b.rng[s], b.draws[s]};
-    mcb::Part<T> q;
-    load_part<T>(b, s, q);
-    unsigned long long* const base = a.tally + b.tbase[s];
-    uint64_t ev = b.events[s];
-    uint32_t co = b.coll[s];
+    Live<T> v;
+    load_live<T>(fin, (uint32_t)t, v);
+    const BoxDev& P = probs[v.prob];
+    mcs::Rng<M> r{v.rng, v.draws};
+    unsigned long long* const base = a.tally + v.tbase;
+    if ((int)v.prob != ec.prob) { ec.flush(a.counts); ec.prob = (int)v.prob; }
     int outcome;
     for (;;) {
-      if (ev == a.event_cap) { outcome = -1; break; }
-      ++ev;
-      const int o = mcb::box_flight<M, T>(P, r, a.lcg, q, base, nullptr, false);
+      if (v.events == a.event_cap) { outcome = -1; break; }
+      ++v.events;
+      ++ec.flights;
+      const int o = mcb::box_flight<M, T>(P, r, a.lcg, v.q, base, planes, false);
       if (o == mcb::kBoxLeak) { outcome = o; break; }
       if (o != mcb::kBoxCollide) continue;  // crossed into the other region
-      ++co;
-      const int c = mcb::box_collide<M, T>(P, r, a.lcg, q);
-      if (c == mcb::kBoxKilled) { outcome = c; break; }
-      if (c >= mcb::kSplitBase + 2) {
-        const uint32_t ns = (uint32_t)(c - mcb::kSplitBase);
-        if ((int)pi != ec.prob) { ec.flush(a.counts); ec.prob = (int)pi; }
-        ++ec.splits;
-        ec.children += ns - 1;
-        for (uint32_t k = 0; k + 1 < ns; ++k) {
-          const unsigned long long idx = atomicAdd(a.child_out_count, 1ull);
-          if (idx < a.child_cap)
-            mcb::store_child<T>(a.child_out[idx], q, mcb::child_seed(k, r.x, a.lcg.mask), pi, b.tbase[s]);
-        }
-      }
+      ++ec.coll;
+      const int cc = mcb::box_collide<M, T>(P, r, a.lcg, v.q);
+      if (cc == mcb::kBoxKilled) { outcome = cc; break; }
+      if (cc >= mcb::kSplitBase + 2) bank_children<T>(a, cc, v.q, r.x, v.prob, v.tbase, ec);
     }
-    b.events[s] = ev;
-    b.coll[s] = co;
-    finish(a, s, outcome, r.x, r.draws, ec);
+    v.rng = r.x;
+    v.draws = r.draws;
+    finish<T>(a, P, v, outcome, ec);
   }
   ec.flush_warp(a.counts);
 }
@@ -375,20 +448,14 @@ __global__ void __launch_bounds__(256) tail_kernel(Args a) {
 constexpr int kIter = 32;
 
 template <int M, typename T>
-void enqueue_batch(const Args& a, int grid, cudaStream_t s) {
-  for (int k = 0; k < kIter; ++k) {
-    plan_kernel<<<1, 1, 0, s>>>(a);
-    refill_kernel<M, T><<<grid, 256, 0, s>>>(a);
-    flight_kernel<M, T><<<grid, 256, 0, s>>>(a);
-    collide_kernel<M, T><<<grid, 256, 0, s>>>(a);
-    advance_kernel<<<1, 1, 0, s>>>(a);
-  }
+void enqueue_batch(const Args<T>& a, int grid, cudaStream_t s) {
+  for (int k = 0; k < kIter; ++k) step_kernel<M, T><<<grid, 256, 0, s>>>(a);
 }
 
 // Runs one generation (sources or children) to completion.
 template <int M, typename T>
-int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_t s) {
-  init_kernel<<<grid, 256, 0, s>>>(a);
+int run_generation(const Args<T>& a, int grid, uint64_t max_batches, const mci::BoxLaunch& L, cudaStream_t s) {
+  init_kernel<M, T><<<grid, 256, 0, s>>>(a);
   MC_TRY_CUDA(cudaGetLastError());
   cudaGraphExec_t exec = nullptr;
   if (L.capture_stream) {
@@ -401,30 +468,13 @@ int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return mci::cuda_status(e, "cudaGraphInstantiate(box event batch)");
   }
-  uint64_t max_batches = (std::min<uint64_t>(L.event_cap, 1ull << 36) * 4 + 64) / kIter +
-                         (a.total / a.b.cap + 2) * 4;
-  if (L.event_iterations != ~0ull)  // a caller's bound (mc_limits), in whole batches
-    max_batches = L.event_iterations / kIter + (L.event_iterations % kIter != 0);
   int st = MC_OK;
   for (uint64_t batch = 0;; ++batch) {
-    if (batch == max_batches) {
-      mci::set_error("box event schedule: no completion after %llu iterations",
-                     (unsigned long long)(batch * kIter));
-      st = MC_ERR_TIMEOUT;
-      break;
-    }
-    cudaError_t e;
-    if (exec) {
-      e = cudaGraphLaunch(exec, s);
-    } else {
-      enqueue_batch<M, T>(a, grid, s);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(L.h_done, &a.b.ctl->done, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+    // the completion flag as the init kernel or the last iteration left it
+    cudaError_t e = cudaMemcpyAsync(L.h_done, &a.b.ctl->done, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-      st = mci::cuda_status(e, "box event batch");
+      st = mci::cuda_status(e, "box event completion check");
       break;
     }
     if (*L.h_done == 2u) {  // the rest of the generation in one kernel
@@ -433,6 +483,22 @@ int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_
       break;
     }
     if (*L.h_done) break;
+    if (batch == max_batches) {
+      mci::set_error("box event schedule: no completion after %llu iterations",
+                     (unsigned long long)(batch * kIter));
+      st = MC_ERR_TIMEOUT;
+      break;
+    }
+    if (exec) {
+      e = cudaGraphLaunch(exec, s);
+    } else {
+      enqueue_batch<M, T>(a, grid, s);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      st = mci::cuda_status(e, "box event batch");
+      break;
+    }
   }
   if (exec) cudaGraphExecDestroy(exec);
   return st;
@@ -440,7 +506,7 @@ int run_generation(const Args& a, int grid, const mci::BoxLaunch& L, cudaStream_
 
 template <int M, typename T>
 int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
-  Args a{};
+  Args<T> a{};
   a.probs = static_cast<const BoxDev*>(L.d_probs);
   a.nprob = L.n_problems;
   a.child_cap = L.child_cap;
@@ -450,9 +516,21 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
   a.hist_draws = L.tally->d_hist_draws;
   a.lcg = mcd::Lcg{L.lcg.g, L.lcg.c, mcd::mask_of(L.lcg.m), L.lcg.m};
   a.event_cap = L.event_cap;
-  carve(L.d_bank, L.bank_cap, &a.b);
-  const int grid = std::max(1, L.num_sms * 4);
-  a.tail_threshold = (uint32_t)L.num_sms * 1024u;
+  carve<T>(L.d_bank, L.bank_cap, &a.b);
+  // One wave of resident blocks: every block of an iteration runs at once.
+  int per_sm = 0;
+  MC_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<M, T>, 256, 0));
+  const int grid = std::max(1, L.num_sms * std::max(per_sm, 1));
+  // Box particles live a few dozen flights: once the ticket is spent, a
+  // half-empty bank is finished faster by the tail kernel than by
+  // iterations of ever fewer particles.
+  a.tail_threshold = std::max<uint32_t>((uint32_t)L.num_sms * 1024u, L.bank_cap / 2);
+  // Each iteration moves every live particle one event and the bank refills
+  // from the ticket; the bound below is a safety net only.
+  uint64_t max_batches = (std::min<uint64_t>(L.event_cap, 1ull << 36) * 4 + 64) / kIter +
+                         (L.total / std::max<uint32_t>(L.bank_cap, 1u) + 2) * 4;
+  if (L.event_iterations != ~0ull)  // a caller's bound (mc_limits), in whole batches
+    max_batches = L.event_iterations / kIter + (L.event_iterations % kIter != 0);
   ChildRec* bank[2] = {static_cast<ChildRec*>(L.d_child[0]), static_cast<ChildRec*>(L.d_child[1])};
   unsigned long long* cnt[2] = {L.d_child_count, L.d_child_count + 1};
   for (uint64_t start = 0; start < L.total; start += L.primary_chunk) {
@@ -463,7 +541,7 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
     a.total = n;
     a.child_out = bank[0];
     a.child_out_count = cnt[0];
-    int st = run_generation<M, T>(a, grid, L, s);
+    int st = run_generation<M, T>(a, grid, max_batches, L, s);
     if (st != MC_OK) return st;
     int cur = 0;
     for (int gen = 1;; ++gen) {
@@ -487,7 +565,7 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
       a.total = made;
       a.child_out = bank[nxt];
       a.child_out_count = cnt[nxt];
-      st = run_generation<M, T>(a, grid, L, s);
+      st = run_generation<M, T>(a, grid, max_batches, L, s);
       if (st != MC_OK) return st;
       cur = nxt;
     }
@@ -499,7 +577,9 @@ int run_box_event(const mci::BoxLaunch& L, cudaStream_t s) {
 
 namespace mci {
 
-size_t box_bank_bytes(uint32_t cap) { return carve(nullptr, cap, nullptr); }
+size_t box_bank_bytes(uint32_t cap) {
+  return std::max(carve<double>(nullptr, cap, nullptr), carve<float>(nullptr, cap, nullptr));
+}
 
 int box_event_run(const BoxLaunch& L, cudaStream_t s) {
   if (L.lcg.m == 63) return L.f32 ? run_box_event<63, float>(L, s) : run_box_event<63, double>(L, s);

@@ -72,6 +72,20 @@ def test_box_event_schedule_bit_identical(env, precision, use_graph):
     assert np.array_equal(h.hist_state.cpu().numpy(), e.hist_state.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_box_event_schedule_refills_a_full_bank(env, precision):
+    """More source histories than the bank's 2^20 slots, so ended slots take
+    new histories (and, in later generations, split children) from the
+    ticket inside the iteration kernel; bits equal the history schedule's."""
+    b = W.box_problem(n_histories=1_200_000, seeding=W.SEED_STRIDE)
+    h = gpu_box(env, b, precision=precision)
+    e = gpu_box(env, b, precision=precision, schedule=1, use_graph=1)
+    assert np.array_equal(h.bins.cpu().numpy(), e.bins.cpu().numpy())
+    assert np.array_equal(counts_of(h), counts_of(e))
+    assert np.array_equal(h.hist_state.cpu().numpy(), e.hist_state.cpu().numpy())
+    assert np.array_equal(h.hist_draws.cpu().numpy(), e.hist_draws.cpu().numpy())
+
+
 @pytest.mark.parametrize("block,chunk", [(64, 1), (128, 32), (512, 256)])
 def test_box_bits_independent_of_launch_shape(env, block, chunk):
     b = W.box_problem(n_histories=20_000, seeding=W.SEED_STRIDE)

@@ -77,7 +77,8 @@ def test_pool_lock_that_never_succeeds_keeps_every_bit(env, precision):
 @pytest.mark.parametrize("use_graph", [0, 1])
 def test_slab_event_schedule_times_out_then_recovers(env, use_graph):
     mc, ctx, torch = env
-    probs = W.slab_small(W.SEED_STRIDE, n_histories=5000)
+    # more histories than the tail kernel takes at once, so iterations are needed
+    probs = W.slab_small(W.SEED_STRIDE, n_histories=400_000)
     ref = slab(mc, ctx, torch, probs)
     mc.mc_ctx_set_limits(ctx, limits(mc, event_iterations=0))
     with pytest.raises(mc.McError) as e:
@@ -115,9 +116,11 @@ def test_box_generations_time_out_then_recover(env, schedule):
         box_run(mc, ctx, torch, b, schedule=schedule)
     assert e.value.status == mc._ffi.MC_ERR_TIMEOUT
     if schedule == 1:
+        # more sources than the tail kernel takes at once: iterations are needed
+        big = W.box_problem(n_histories=200_000, seeding=W.SEED_HASH)
         mc.mc_ctx_set_limits(ctx, limits(mc, event_iterations=0))
         with pytest.raises(mc.McError) as e:
-            box_run(mc, ctx, torch, b, schedule=schedule)
+            box_run(mc, ctx, torch, big, schedule=schedule)
         assert e.value.status == mc._ffi.MC_ERR_TIMEOUT
     mc.mc_ctx_set_limits(ctx, None)
     got = box_run(mc, ctx, torch, b, schedule=schedule)

@@ -315,6 +315,19 @@ def test_event_schedule_bit_identical_to_history(env, oracle, precision, use_gra
         assert_tally_close(ev.bins.cpu().numpy(), o["tally"])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_event_schedule_refills_a_full_bank(env, precision):
+    """More histories than the bank's 2^20 slots: ended slots take new
+    histories from the ticket inside the iteration kernel for many
+    iterations before the tail kernel; the bits equal the history
+    schedule's."""
+    probs = W.slab_small(W.SEED_STRIDE, n_histories=1_500_000)
+    hist, _ = gpu_run(env, probs, precision=precision)
+    for use_graph in (0, 1):
+        ev, _ = gpu_run(env, probs, precision=precision, schedule=1, use_graph=use_graph)
+        _same_bits(hist, ev, 1)
+
+
 def test_event_schedule_event_cap_and_ranges(env):
     mc, ctx, torch = env
     p = [W.slab_problem(200.0, 1.0, 0.9999, 300, 10, 1, W.SEED_HASH)]
