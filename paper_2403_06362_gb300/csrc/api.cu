@@ -258,7 +258,7 @@ int check_problems(const mc_problem* p, uint32_t n, const mc_tally* t, uint64_t*
 }
 
 constexpr uint64_t kChildCap = 1ull << 22;      // child records per bank
-constexpr uint64_t kPrimaryChunk = 1ull << 21;  // source histories per generation-0 launch
+constexpr uint64_t kPrimaryChunk = 1ull << 22;  // source histories per generation-0 launch
 
 int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_config* cfg, const mc_tally* tally,
             uint64_t rb, uint64_t re, unsigned long long* ticket, cudaStream_t s) {
@@ -293,7 +293,8 @@ int run_box(mc_ctx* ctx, const mc_lcg* lcg, uint32_t n_problems, const mc_run_co
   L.tally_agg = mci::tally_agg_of(cfg->tally_atomics, mci::kBoxAggDefault);
   L.event_iterations = ctx->limits.event_iterations;
   if (cfg->schedule == MC_SCHED_EVENT) {
-    const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.total, 1), 1u << 20);
+    // Two banks of up to 2^21 particles (about 0.55 GiB fp64); allocated on first use.
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(std::max<uint64_t>(L.total, 1), 1u << 21);
     st = ctx->bank.reserve(mci::box_bank_bytes(cap));
     if (st != MC_OK) return st;
     if (!ctx->h_done) MC_TRY_CUDA(cudaMallocHost(&ctx->h_done, sizeof(unsigned int)));
@@ -643,8 +644,8 @@ int transport_run_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problem
   st = make_slab_launch(ctx, lcg, problems, n_problems, cfg, tally, rb, re, ticket, &L);
   if (st != MC_OK) return st;
   if (cfg->schedule == MC_SCHED_EVENT) {
-    // Bank of up to 2^20 particles (about 100 MiB); allocated on first use.
-    const uint32_t cap = (uint32_t)std::min<uint64_t>(L.total, 1u << 20);
+    // Two banks of up to 2^21 particles (about 0.35 GiB fp64); allocated on first use.
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(L.total, 1u << 21);
     st = ctx->bank.reserve(mci::slab_bank_bytes(cap));
     if (st != MC_OK) return st;
     if (!ctx->h_done) MC_TRY_CUDA(cudaMallocHost(&ctx->h_done, sizeof(unsigned int)));

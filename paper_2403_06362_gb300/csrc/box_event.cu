@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) init_kernel(Args<T> a) {
 // particles, go to the other bank.  The last block to finish advances the
 // control block.
 template <int M, typename T>
-__global__ void __launch_bounds__(256, 3) step_kernel(Args<T> a) {
+__global__ void __launch_bounds__(256, 4) step_kernel(Args<T> a) {
   __shared__ __align__(16) SharedProblem<T> sp;
   const double* planes = nullptr;
   const BoxDev* probs = stage_problem<T>(a, sp, &planes);

@@ -74,10 +74,10 @@ def test_box_event_schedule_bit_identical(env, precision, use_graph):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_box_event_schedule_refills_a_full_bank(env, precision):
-    """More source histories than the bank's 2^20 slots, so ended slots take
+    """More source histories than the bank's 2^21 slots, so ended slots take
     new histories (and, in later generations, split children) from the
     ticket inside the iteration kernel; bits equal the history schedule's."""
-    b = W.box_problem(n_histories=1_200_000, seeding=W.SEED_STRIDE)
+    b = W.box_problem(n_histories=2_500_000, seeding=W.SEED_STRIDE)
     h = gpu_box(env, b, precision=precision)
     e = gpu_box(env, b, precision=precision, schedule=1, use_graph=1)
     assert np.array_equal(h.bins.cpu().numpy(), e.bins.cpu().numpy())

@@ -317,11 +317,11 @@ def test_event_schedule_bit_identical_to_history(env, oracle, precision, use_gra
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_event_schedule_refills_a_full_bank(env, precision):
-    """More histories than the bank's 2^20 slots: ended slots take new
+    """More histories than the bank's 2^21 slots: ended slots take new
     histories from the ticket inside the iteration kernel for many
     iterations before the tail kernel; the bits equal the history
     schedule's."""
-    probs = W.slab_small(W.SEED_STRIDE, n_histories=1_500_000)
+    probs = W.slab_small(W.SEED_STRIDE, n_histories=3_000_000)
     hist, _ = gpu_run(env, probs, precision=precision)
     for use_graph in (0, 1):
         ev, _ = gpu_run(env, probs, precision=precision, schedule=1, use_graph=use_graph)
