@@ -58,6 +58,21 @@ E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 DRAW_KERNEL_TRAFFIC_BYTES = 1.013e9
 # Streams of the materialised-uniform leg (fp64 uniforms stored, draw-major).
 N_STREAMS_MATERIALISED = 2**22
+# Executed thread instructions per flight of each transport kernel as built
+# (ncu smsp__thread_inst_executed over every launch of a run, divided by its
+# flights; profiles/transport_kernels_instructions_per_flight.md).  Times the
+# measured flights/s, they place a transport workload against the issue peak.
+INST_PER_FLIGHT = {
+    "slab_small_fp64": 777, "slab_small_fp32": 549, "slab_long_fp64": 605, "slab_long_fp32": 387,
+    "batched_fp64": 674, "batched_fp32": 435, "box_fp64": 2292, "box_fp32": 881,
+    "box_fp64_event": 2697, "box_fp32_event": 1269,
+    "pulse_hash": 366, "pulse_stride": 351, "pulse_census": 252,
+}
+# Bytes each flight of an event schedule moves through its particle bank: the
+# particle's fields read and written once per iteration (slab: x, mu, w, the
+# stream, draw and flight counts, history index, tally row, problem; box: the
+# position, direction, inverse direction, weight and the same bookkeeping).
+EVENT_BANK_BYTES_PER_FLIGHT = {"slab_fp64": 2 * 68, "slab_fp32": 2 * 56, "box_fp64": 2 * 128, "box_fp32": 2 * 88}
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 
@@ -235,7 +250,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-detail", action="store_true")
     ap.add_argument("--profile-workload", default=None,
-                    choices=["slab_long_fp64", "slab_long_fp32", "slab_small_fp64", "box_fp32", "box_fp64",
+                    choices=["slab_long_fp64", "slab_long_fp32", "slab_small_fp64", "slab_small_fp32", "box_fp32", "box_fp64",
                              "batched_fp32", "batched_fp64", "pulse_hash", "pulse_stride", "pulse_census"],
                     help="run one transport workload (a warm-up run, then one run) and exit; for profilers")
     ap.add_argument("--histories", type=int, default=0, help="history count for --profile-workload")
@@ -451,8 +466,8 @@ def profile_workload(args):
         b2.record()
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b2))
-    r = mc.mc_tally_read(ctx, cp, 0, tally.c, check=False)
-    print(json.dumps({"workload": name, "histories": n, "ms": times[-1], "flights": r.counts["flights"]}))
+    flights = int(tally.counts.view(-1, 17)[:, 1].sum().item())  # over every problem
+    print(json.dumps({"workload": name, "histories": n, "ms": times[-1], "flights": flights}))
     del keep
     ctx.close()
 
@@ -547,10 +562,31 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             best = ms if best is None else min(best, ms)
         return best, tally, cp
 
-    def entry(ms, tally, cp, n, idx=0):
+    peaks, peak_src = measured_peaks()
+    issue_peak = int_issue_peak(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+    def issue_roofline(flights_per_s, key):
+        ops = INST_PER_FLIGHT[key]
+        ach = flights_per_s * ops
+        return {"bound": "issue", "achieved": ach / 1e12, "peak": issue_peak / 1e12, "unit": "Tops/s",
+                "frac": ach / issue_peak, "ops_per_flight": ops,
+                "ops_note": "executed thread instructions per flight (ncu); derived issue peak"}
+
+    def bank_roofline(flights_per_s, key):
+        b = EVENT_BANK_BYTES_PER_FLIGHT[key]
+        gbs = flights_per_s * b / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "bytes_per_flight": b, "peak_source": peak_src,
+                "note": "particle bank read and written once per flight; not the bound (see DESIGN)"}
+
+    def entry(ms, tally, cp, n, idx=0, key=None):
         r = mc.mc_tally_read(ctx, cp, idx, tally.c, stream, check=False)
-        return {"ms": ms, "histories_per_s": n / (ms / 1e3), "flights_per_s": r.counts["flights"] / (ms / 1e3),
-                "exceed_hist": r.counts["exceed_hist"], "max_draws": r.counts["max_draws"]}
+        flights = int(tally.counts.view(-1, 17)[:, 1].sum().item())  # over every problem
+        e = {"ms": ms, "histories_per_s": n / (ms / 1e3), "flights_per_s": flights / (ms / 1e3),
+             "exceed_hist": r.counts["exceed_hist"], "max_draws": r.counts["max_draws"]}
+        if key is not None:
+            e["roofline"] = issue_roofline(flights / (ms / 1e3), key)
+        return e
 
     for name, fn in (("slab_small", W.slab_small), ("slab_long", W.slab_long)):
         for sname, sd in (("hash", W.SEED_HASH), ("stride", W.SEED_STRIDE)):
@@ -558,7 +594,7 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             n = p[0]["n_histories"]
             for prec in (0, 1):
                 ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, precision=prec)
-                e = entry(ms, tally, cp, n)
+                e = entry(ms, tally, cp, n, key=f"{name}_{'fp32' if prec else 'fp64'}")
                 if prec == 0:
                     hist_bins = tally.bins.clone()
                     r64 = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
@@ -574,6 +610,7 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                 res[f"{name}_{sname}_{'fp32' if prec else 'fp64'}"] = e
             ms, tally, cp = timed(p, reps=1, precision=0, schedule=1, use_graph=1)
             e = entry(ms, tally, cp, n)
+            e["roofline"] = bank_roofline(e["flights_per_s"], "slab_fp64")
             e["bits_identical_to_history"] = bool(torch.equal(tally.bins, hist_bins))
             res[f"{name}_{sname}_fp64_event"] = e
 
@@ -645,6 +682,10 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                            "fp32_vs_fp64_bin_rel_diff": {"max": float(rel.max()), "median": float(np.median(rel)),
                                                          "bins": int(rel.size)},
                            "fp32_histories_diverged": diverged}
+    fl32 = int(t32.counts.view(-1, 17)[:, 1].sum().item())
+    fl64 = int(t64.counts.view(-1, 17)[:, 1].sum().item())
+    res["slab_batched"]["roofline_fp32"] = issue_roofline(fl32 / (ms32 / 1e3), "batched_fp32")
+    res["slab_batched"]["roofline_fp64"] = issue_roofline(fl64 / (ms64 / 1e3), "batched_fp64")
 
     # Section 5 experiment: 30 repetitions x 1000 batches x 1000 sources, hash
     # (hierarchical seeds) vs stride; Shapiro-Wilk on each of the 20 points
@@ -674,7 +715,10 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             "ms": ms, "source_histories_per_s": n / (ms / 1e3), "collisions_per_s": r.counts["collisions"] / (ms / 1e3),
             "census_per_source": r.counts["leak_hi"] / n, "secondaries": r.counts["children"],
             "sw_fails_p_lt_0.05": int(np.sum(pvals < 0.05)), "sw_tests": int(pvals.size),
-            "sw_median_p_per_point": [float(v) for v in np.median(pvals, axis=0)]}
+            "sw_median_p_per_point": [float(v) for v in np.median(pvals, axis=0)],
+            "roofline": issue_roofline(r.counts["flights"] / (ms / 1e3),
+                                       {"hash": "pulse_hash", "stride": "pulse_stride",
+                                        "census_hash": "pulse_census"}[sname])}
         if nc:
             res[f"pulse_paper_{sname}"].update(
                 n_census=nc, flights=r.counts["flights"], banked=r.counts["banked"],
@@ -692,7 +736,10 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
     for label, kw in (("fp32_history", dict(precision=1)), ("fp32_event", dict(precision=1, schedule=1, use_graph=1)),
                       ("fp64_history", dict(precision=0)), ("fp64_event", dict(precision=0, schedule=1, use_graph=1))):
         ms, tally, cp = timed(None, reps=1, box=box, **kw)
-        e = entry(ms, tally, cp, n)
+        prec = "fp32" if label.startswith("fp32") else "fp64"
+        e = entry(ms, tally, cp, n, key=f"box_{prec}" + ("_event" if "event" in label else ""))
+        if "event" in label:
+            e["roofline_bank"] = bank_roofline(e["flights_per_s"], f"box_{prec}")
         r = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
         e.update(children=r.counts["children"], splits=r.counts["splits"], roulette_kills=r.counts["roulette_kills"])
         bits[label] = tally.bins.clone()

@@ -46,8 +46,8 @@ struct Ctl {
   unsigned long long iters;
 };
 
-// One bank: an array per field.  T = float: 92 bytes per particle;
-// T = double: 132.
+// One bank: an array per field.  T = float: 88 bytes per particle;
+// T = double: 128.
 template <typename T>
 struct SoA {
   T *p[3], *u[3], *inv[3], *w;
