@@ -72,7 +72,7 @@ INST_PER_FLIGHT = {
 # particle's fields read and written once per iteration (slab: x, mu, w, the
 # stream, draw and flight counts, history index, tally row, problem; box: the
 # position, direction, inverse direction, weight and the same bookkeeping).
-EVENT_BANK_BYTES_PER_FLIGHT = {"slab_fp64": 2 * 68, "slab_fp32": 2 * 56, "box_fp64": 2 * 128, "box_fp32": 2 * 88}
+EVENT_BANK_BYTES_PER_FLIGHT = {"slab_fp64": 2 * 68, "slab_fp32": 2 * 60, "box_fp64": 2 * 128, "box_fp32": 2 * 88}
 RECIPE_SM_MAX_MHZ = 2070.0
 LANES_PER_SM_PER_CLK = 128  # 4 sub-partitions x 1 warp instruction x 32 lanes
 
@@ -539,7 +539,7 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
     Section 5 normality procedure on the batch means, hash vs stride."""
     res = {}
 
-    def timed(probs, reps=2, box=None, keep=False, **cfgkw):
+    def timed(probs, reps=2, box=None, keep=False, hist=False, **cfgkw):
         if box is not None:
             prob, spec = W.to_mc_box(box, mc)
             cp = mc.problem_array([prob])
@@ -547,7 +547,8 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             tally._keep = spec
         else:
             cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
-            tally = mc.Tally(W.tally_slots(probs), len(probs))
+            tally = mc.Tally(W.tally_slots(probs), len(probs),
+                             n_histories=sum(q["n_histories"] for q in probs) if hist else 0)
         cfg = mc.mc_run_config(**cfgkw)
         mc.mc_transport_run(ctx, lcg, cp, cfg, tally.c, stream)
         torch.cuda.synchronize()
@@ -593,10 +594,11 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
             p = fn(sd)
             n = p[0]["n_histories"]
             for prec in (0, 1):
-                ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, precision=prec)
+                ms, tally, cp = timed(p, reps=3 if name == "slab_small" else 1, hist=True, precision=prec)
                 e = entry(ms, tally, cp, n, key=f"{name}_{'fp32' if prec else 'fp64'}")
                 if prec == 0:
                     hist_bins = tally.bins.clone()
+                    hist_state64 = tally.hist_state.clone()
                     r64 = mc.mc_tally_read(ctx, cp, 0, tally.c, stream, check=False)
                 else:
                     # fp32-guarded flux against the fp64 flux, per bin: relative
@@ -607,6 +609,9 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                     se = r64.rel_err * f64
                     e["fp32_vs_fp64_rel_diff_max"] = float(np.max(np.where(f64 > 0, d / np.where(f64 > 0, f64, 1), 0)))
                     e["fp32_vs_fp64_diff_in_se_max"] = float(np.max(np.where(se > 0, d / np.where(se > 0, se, 1), 0)))
+                    # histories whose fp32 run ended in another state: a
+                    # decision went the other way somewhere in them
+                    e["fp32_histories_diverged"] = int((tally.hist_state != hist_state64).sum().item())
                 res[f"{name}_{sname}_{'fp32' if prec else 'fp64'}"] = e
             ms, tally, cp = timed(p, reps=1, precision=0, schedule=1, use_graph=1)
             e = entry(ms, tally, cp, n)
@@ -748,6 +753,15 @@ def transport_detail(mc, ctx, lcg, torch, dev, stream, W):
                                                                                       bits["fp32_history"]))
     res["box_large_hash_fp64_event"]["bits_identical_to_history"] = bool(torch.equal(bits["fp64_event"],
                                                                                       bits["fp64_history"]))
+    # fp32-guarded mesh against fp64, voxel by voxel (the box's fp32 path keeps
+    # plain fp32 positions)
+    m32 = bits["fp32_history"].cpu().numpy().astype(np.float64)
+    m64 = bits["fp64_history"].cpu().numpy().astype(np.float64)
+    nz = m64 != 0
+    vrel = np.abs(m32[nz] - m64[nz]) / np.abs(m64[nz])
+    res["box_large_hash_fp32_history"]["fp32_vs_fp64_voxel_rel_diff"] = {
+        "max": float(vrel.max()), "median": float(np.median(vrel)), "voxels": int(vrel.size),
+        "total_rel_diff": float(abs(m32.sum() - m64.sum()) / m64.sum())}
     del bits
     return res
 

@@ -278,7 +278,7 @@ __device__ __forceinline__ int box_flight(const BoxDev& b, mcs::Rng<M>& r, const
     collide = lt(d, ds);
   } else {
     const double u = r.next(l);
-    d = -log1pf(-(float)u) * b.inv_st_f[q.region];
+    d = mcs::flight_f32(u) * b.inv_st_f[q.region];
     collide = d < ds;
     if (fabsf(d - ds) <= 0x1p-16f * fmaxf(d, ds)) {  // near the surface: decide in fp64
       Part<double> q64;

@@ -97,7 +97,7 @@ struct RunArgs {
 // by one lane per warp, with bounded attempts; a warp that cannot take it
 // skips the hand-over (or, leaving, counts the stranded particles in
 // MC_C_DROPPED, the error the host reports).
-constexpr int kPoolWords = 9;
+constexpr int kPoolWords = 10;
 struct PoolCtl {
   int lock, n, active, pad;
 };
@@ -128,6 +128,7 @@ __device__ __forceinline__ void pool_put(unsigned long long* e, const mcs::Rng<M
   e[6] = ((unsigned long long)pi << 32) | __float_as_uint(q.wf);
   e[7] = gi;
   e[8] = events;
+  e[9] = __float_as_uint(q.xlo);
 }
 
 template <int M>
@@ -143,6 +144,7 @@ __device__ __forceinline__ uint32_t pool_get(const unsigned long long* e, mcs::R
   q.wf = __uint_as_float((uint32_t)e[6]);
   gi = e[7];
   events = e[8];
+  q.xlo = __uint_as_float((uint32_t)e[9]);
   return (uint32_t)(e[6] >> 32);
 }
 

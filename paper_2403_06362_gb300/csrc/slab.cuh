@@ -196,14 +196,25 @@ __device__ __forceinline__ float slab_edge_f(const SlabDev& p, int j) {
   return j >= (int)p.n_bins ? p.L_f : (float)j * p.h_f;
 }
 
-__device__ __forceinline__ void seg32(const SlabDev& p, float a, float b, float w_mu, const Sink& s) {
+// Track length of the segment [a, b] in every bin it meets, the ends given
+// as pairs (ah + al, bh + bl) of the fp32 path.  Each bin's length is taken
+// from the pairs, (hi_h - lo_h) + (hi_l - lo_l), so a flight whose
+// displacement is far below an ulp of its position (a direction nearly
+// parallel to the faces, where 1 / |mu| is large) keeps its true length
+// instead of an ulp of the position times 1 / |mu|.
+__device__ __forceinline__ void seg32(const SlabDev& p, float ah, float al, float bh, float bl, float w_mu,
+                                      const Sink& s) {
   const int nb = (int)p.n_bins;
-  const int j0 = clamp_bin((int)(a * p.inv_h_f) - 1, nb);
-  const int j1 = clamp_bin((int)(b * p.inv_h_f) + 1, nb);
+  const int j0 = clamp_bin((int)(ah * p.inv_h_f) - 1, nb);
+  const int j1 = clamp_bin((int)(bh * p.inv_h_f) + 1, nb);
   for (int j = j0; j <= j1; ++j) {
     const float lo_e = slab_edge_f(p, j), hi_e = slab_edge_f(p, j + 1);
-    const float lo = fmaxf(a, lo_e), hi = fminf(b, hi_e);
-    if (hi > lo) s.add(j, fix32_from_float((hi - lo) * w_mu));
+    // max(a, lo_e) and min(b, hi_e) as pairs (an edge's low part is zero)
+    float loh = lo_e, lol = 0.0f, hih = hi_e, hil = 0.0f;
+    if (ah > lo_e || (ah == lo_e && al > 0.0f)) { loh = ah; lol = al; }
+    if (bh < hi_e || (bh == hi_e && bl < 0.0f)) { hih = bh; hil = bl; }
+    const float len = __fadd_rn(__fsub_rn(hih, loh), __fsub_rn(hil, lol));
+    if (len > 0.0f) s.add(j, fix32_from_float(__fmul_rn(len, w_mu)));
   }
 }
 
@@ -217,11 +228,34 @@ __device__ __forceinline__ void point32(const SlabDev& p, float x, float d, cons
 
 // Particle state of the slab physics.  fp64 path: x, mu and w_mu, which
 // holds 2^32 / |mu| (0 for mu = 0); the fp32 path keeps its geometry in
-// xf, muf and wf = 1 / |muf|.
+// fp32: the position as an unevaluated sum xf + xlo of two floats (so that
+// it does not drift from the fp64 trajectory by one rounding per flight),
+// muf and wf = 1 / |muf|.
 struct SlabParticle {
   double x, mu, w_mu;
-  float xf, muf, wf;
+  float xf, xlo, muf, wf;
 };
+
+// s + t = a + b exactly (Knuth's TwoSum; six fp32 operations, no fused
+// multiply-add, so every one rounds once).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// -ln(1 - u) in fp32 for u in [0, 1): log1pf(-u) below 1/2 (no
+// cancellation for small u), else logf of 1 - u, which is exact in fp64 and
+// at least 2^-53, so it rounds to a positive float and the result is finite
+// (log1pf of -(float)u would meet -1 and give an infinite distance for u
+// within 2^-25 of 1).
+__device__ __forceinline__ float flight_f32(double u) {
+  return u < 0.5 ? -log1pf(-(float)u) : -logf(__double2float_rn(__dsub_rn(1.0, u)));
+}
+
+// The fp32 direction 2u - 1 for u = n 2^-53: the exact fp64 value rounded
+// once to fp32.
+__device__ __forceinline__ float mu_f32(uint64_t n) { return __double2float_rn(mcx::two_u_minus_1(n)); }
 
 // 2^32 / |mu| rounded once: 2^32 RN(1 / |mu|), the reciprocal on the
 // integer pipes (fp_exact.cuh), the scaling an exponent add.
@@ -293,7 +327,7 @@ template <int M, bool F32>
 __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const mcd::Lcg& l, SlabParticle& q) {
   if (p.source == MC_SRC_BEAM) {
     q.x = 0.0; q.mu = 1.0; q.w_mu = kFix;
-    q.xf = 0.0f; q.muf = 1.0f; q.wf = 1.0f;
+    q.xf = 0.0f; q.xlo = 0.0f; q.muf = 1.0f; q.wf = 1.0f;
     return;
   }
   const double u1 = r.next(l);
@@ -302,9 +336,11 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
     q.mu = mcx::two_u_minus_1(r.next_n(l));
     q.w_mu = fix_per_mu(q.mu);
   } else {
-    const double u2 = r.next(l);
-    q.xf = p.L_f * (float)u1;
-    q.muf = 2.0f * (float)u2 - 1.0f;
+    // x = L u as the fp64 path has it, split into two floats
+    const double x64 = __dmul_rn(p.L, u1);
+    q.xf = __double2float_rn(x64);
+    q.xlo = __double2float_rn(__dsub_rn(x64, (double)q.xf));
+    q.muf = mu_f32(r.next_n(l));
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
   }
 }
@@ -329,30 +365,43 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
     q.x = xn;
   } else {
     const double u = r.next(l);
-    const float d = -log1pf(-(float)u) * p.inv_st_f;
-    float xn = fmaf(d, q.muf, q.xf);
+    const float d = flight_f32(u) * p.inv_st_f;
+    // xn + xnlo = (xf + xlo) + d muf: the product's exact error from a fused
+    // multiply-add, the sum by TwoSum; the low parts' sum rounds once more,
+    // a second-order error.
+    const float pr = __fmul_rn(d, q.muf);
+    const float pe = __fmaf_rn(d, q.muf, -pr);
+    float s0, t0;
+    two_sum_f(q.xf, pr, s0, t0);
+    float xn, xnlo;
+    two_sum_f(s0, __fadd_rn(t0, __fadd_rn(q.xlo, pe)), xn, xnlo);
     // Guard band: re-decide leak vs collide in fp64 near a face.
     const bool near_hi = q.muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
     const bool near_lo = q.muf < 0.0f && fabsf(xn) <= p.guard_f;
-    bool leak_hi = q.muf > 0.0f && xn >= p.L_f, leak_lo = q.muf < 0.0f && xn <= 0.0f;
+    // xn + xnlo >= L (or <= 0) from the pair: the low part decides a tie of the high part
+    bool leak_hi = q.muf > 0.0f && (xn > p.L_f || (xn == p.L_f && xnlo >= 0.0f));
+    bool leak_lo = q.muf < 0.0f && (xn < 0.0f || (xn == 0.0f && xnlo <= 0.0f));
     if (near_hi || near_lo) {
       const double d64 = __dmul_rn(-mclog::log1m(u), p.inv_st);
-      const double xn64 = __dadd_rn((double)q.xf, __dmul_rn(d64, (double)q.muf));
+      const double x64 = __dadd_rn((double)q.xf, (double)q.xlo);
+      const double xn64 = __dadd_rn(x64, __dmul_rn(d64, (double)q.muf));
       leak_hi = q.muf > 0.0f && xn64 >= p.L;
       leak_lo = q.muf < 0.0f && xn64 <= 0.0;
-      xn = (float)xn64;
+      xn = __double2float_rn(xn64);
       if (!leak_hi && !leak_lo) {
-        // keep the collision site strictly inside after rounding to fp32
+        // keep the collision site's high part strictly inside
         if (xn >= p.L_f) xn = __int_as_float(__float_as_int(p.L_f) - 1);
         if (xn <= 0.0f) xn = 1.0e-30f;
       }
+      xnlo = __double2float_rn(__dsub_rn(xn64, (double)xn));
     }
-    if (leak_hi) { seg32(p, q.xf, p.L_f, q.wf, s); return kLeakHi; }
-    if (leak_lo) { seg32(p, 0.0f, q.xf, q.wf, s); return kLeakLo; }
+    if (leak_hi) { seg32(p, q.xf, q.xlo, p.L_f, 0.0f, q.wf, s); return kLeakHi; }
+    if (leak_lo) { seg32(p, 0.0f, 0.0f, q.xf, q.xlo, q.wf, s); return kLeakLo; }
     if (q.muf == 0.0f) point32(p, q.xf, d, s);
-    else if (q.muf > 0.0f) seg32(p, q.xf, xn, q.wf, s);
-    else seg32(p, xn, q.xf, q.wf, s);
+    else if (q.muf > 0.0f) seg32(p, q.xf, q.xlo, xn, xnlo, q.wf, s);
+    else seg32(p, xn, xnlo, q.xf, q.xlo, q.wf, s);
     q.xf = xn;
+    q.xlo = xnlo;
   }
   return kCollide;
 }
@@ -366,8 +415,7 @@ __device__ __forceinline__ int slab_collide(const SlabDev& p, Rng<M>& r, const m
     q.mu = mcx::two_u_minus_1(r.next_n(l));
     q.w_mu = fix_per_mu(q.mu);
   } else {
-    const double u2 = r.next(l);
-    q.muf = 2.0f * (float)u2 - 1.0f;
+    q.muf = mu_f32(r.next_n(l));
     q.wf = q.muf != 0.0f ? __frcp_rn(fabsf(q.muf)) : 0.0f;
   }
   return kContinue;

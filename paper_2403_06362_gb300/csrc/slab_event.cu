@@ -50,7 +50,7 @@ struct EvCtl {
 // fp32 path's xf, muf and 1/|muf|, then the stream, its draw and flight
 // counts, the history index, the tally row, the problem and, in launches of
 // several problems, the history's collision and scattering counts so far
-// (68 + 16 bytes fp64, 56 + 16 fp32 per particle).  There a history's counters
+// (68 + 16 bytes fp64, 60 + 16 fp32 per particle).  There a history's counters
 // are added to its problem's when it ends, so a pass touches the counters
 // once per ended history, not once per event; a single problem's lanes count
 // every event in registers.
@@ -58,6 +58,7 @@ template <bool F32>
 struct EvSoA {
   using P = typename std::conditional<F32, float, double>::type;
   P *x, *mu, *w;
+  float* xlo;  // fp32 path: the low part of the position
   uint64_t *rng, *draws, *events, *gi, *tbase;
   uint32_t* prob;
   uint64_t *coll, *scat;
@@ -115,6 +116,7 @@ size_t carve(void* base, uint32_t cap, EvBank<F32>* b) {
     f.x = reinterpret_cast<P*>(take((size_t)cap * sizeof(P)));
     f.mu = reinterpret_cast<P*>(take((size_t)cap * sizeof(P)));
     f.w = reinterpret_cast<P*>(take((size_t)cap * sizeof(P)));
+    f.xlo = F32 ? reinterpret_cast<float*>(take((size_t)cap * 4)) : nullptr;
     uint64_t** uu[] = {&f.rng, &f.draws, &f.events, &f.gi, &f.tbase};
     for (uint64_t** u : uu) *u = reinterpret_cast<uint64_t*>(take((size_t)cap * 8));
     f.prob = reinterpret_cast<uint32_t*>(take((size_t)cap * 4));
@@ -137,7 +139,7 @@ template <bool F32>
 __device__ __forceinline__ void load_live(const EvSoA<F32>& f, uint32_t s, EvLive& v, bool per_hist) {
   v.q = mcs::SlabParticle{};
   if constexpr (F32) {
-    v.q.xf = f.x[s]; v.q.muf = f.mu[s]; v.q.wf = f.w[s];
+    v.q.xf = f.x[s]; v.q.xlo = f.xlo[s]; v.q.muf = f.mu[s]; v.q.wf = f.w[s];
   } else {
     v.q.x = f.x[s]; v.q.mu = f.mu[s]; v.q.w_mu = f.w[s];
   }
@@ -154,7 +156,7 @@ __device__ __forceinline__ void load_live(const EvSoA<F32>& f, uint32_t s, EvLiv
 template <bool F32>
 __device__ __forceinline__ void store_live(const EvSoA<F32>& f, uint32_t s, const EvLive& v, bool per_hist) {
   if constexpr (F32) {
-    f.x[s] = v.q.xf; f.mu[s] = v.q.muf; f.w[s] = v.q.wf;
+    f.x[s] = v.q.xf; f.xlo[s] = v.q.xlo; f.mu[s] = v.q.muf; f.w[s] = v.q.wf;
   } else {
     f.x[s] = v.q.x; f.mu[s] = v.q.mu; f.w[s] = v.q.w_mu;
   }
