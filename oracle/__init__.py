@@ -132,7 +132,7 @@ def lib():
             L.or_azurv1_run.restype = C.c_int
             L.or_azurv1_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, P, P]
             L.or_azurv1_census_run.restype = C.c_int
-            L.or_azurv1_census_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, C.c_int, P]
+            L.or_azurv1_census_run.argtypes = [C.POINTER(Lcg), AP, u64, u64, u64, P, P, C.c_int, P, P]
             L.or_norm_cdf.restype = dbl; L.or_norm_cdf.argtypes = [dbl]
             L.or_norm_ppf.restype = dbl; L.or_norm_ppf.argtypes = [dbl]
             L.or_shapiro_wilk.restype = C.c_int
@@ -376,8 +376,8 @@ def azurv1_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, event_cap=2
 def azurv1_census_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, event_cap=2**62, tally=None,
                       counts=None, reverse=False, populations=False):
     """Census phases with population control; g_begin, g_end on group
-    boundaries.  populations: also return the particles starting each phase,
-    per group ([groups, n_census])."""
+    boundaries.  populations: also return the particles starting each phase
+    and the weight each of them carries, per group ([groups, n_census])."""
     total = int(prob.n_reps) * int(prob.n_batches) * int(prob.per_batch)
     if g_end is None:
         g_end = total
@@ -388,9 +388,10 @@ def azurv1_census_run(lcg: Lcg, prob: Azurv1Problem, g_begin=0, g_end=None, even
         counts = np.zeros(NCOUNT, dtype=np.uint64)
     groups = (g_end - g_begin) // int(prob.per_batch)
     pop = np.zeros((groups, int(prob.n_census)), dtype=np.uint64) if populations else None
+    wph = np.zeros((groups, int(prob.n_census)), dtype=np.float64) if populations else None
     st = lib().or_azurv1_census_run(C.byref(lcg), C.byref(prob), g_begin, g_end, event_cap, _ptr(tally),
-                                    _ptr(counts), 1 if reverse else 0, _ptr(pop))
-    return dict(status=st, tally=tally, counts=counts, populations=pop)
+                                    _ptr(counts), 1 if reverse else 0, _ptr(pop), _ptr(wph))
+    return dict(status=st, tally=tally, counts=counts, populations=pop, weights=wph)
 
 
 def azurv1_seed(lcg: Lcg, prob: Azurv1Problem, g: int) -> int:

@@ -118,7 +118,8 @@ int or_azurv1_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin,
 /* Census phases with population control by one-off hashed values
  * (mc_oracle_census.c); g_begin, g_end multiples of per_batch, hash seeding. */
 int or_azurv1_census_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
-                         uint64_t event_cap, int64_t* tally, uint64_t* counts, int reverse, uint64_t* pop);
+                         uint64_t event_cap, int64_t* tally, uint64_t* counts, int reverse, uint64_t* pop,
+                         double* wphase);
 
 double or_norm_cdf(double z);
 double or_norm_ppf(double p);

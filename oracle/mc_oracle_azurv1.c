@@ -71,7 +71,7 @@ uint64_t or_azurv1_seed(const or_lcg* l, const or_azurv1_problem* a, uint64_t g)
 int or_azurv1_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
                   uint64_t event_cap, int64_t* tally, uint64_t* counts, uint64_t* hist_state,
                   uint64_t* hist_draws) {
-    if (a->n_census >= 2) return or_azurv1_census_run(l, a, g_begin, g_end, event_cap, tally, counts, 0, NULL);
+    if (a->n_census >= 2) return or_azurv1_census_run(l, a, g_begin, g_end, event_cap, tally, counts, 0, NULL, NULL);
     const int hash_mode = a->seeding != OR_SEED_STRIDE;
     const double inv_st = 1.0 / a->sigma_t;
     const int64_t unit = llrint(inv_st * 4294967296.0);

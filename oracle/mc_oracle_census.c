@@ -42,7 +42,9 @@
  * The result does not depend on the order in which particles are followed
  * or banked: `reverse` != 0 follows every list backwards (a test of that
  * property).  `pop` (nullable) receives, per group and phase, the number of
- * particles that start the phase: pop[(group - first group) * C + p - 1].
+ * particles that start the phase: pop[(group - first group) * C + p - 1];
+ * `wphase` (nullable) the weight every one of them carries (1 in phase 1,
+ * Wd / N after each control), in the same layout.
  */
 #include <math.h>
 #include <stdint.h>
@@ -180,8 +182,8 @@ static int cz_follow(const or_lcg* l, const or_azurv1_problem* a, cz_part e, dou
 
 /* Population control of one group's bank at the end of phase p (Section 4,
  * one-off values; Eq. 5 for the copies' streams). */
-static void cz_control(const or_lcg* l, const or_azurv1_problem* a, uint32_t p, const cz_list* bank,
-                       cz_list* next, uint64_t* counts, int reverse) {
+static double cz_control(const or_lcg* l, const or_azurv1_problem* a, uint32_t p, const cz_list* bank,
+                         cz_list* next, uint64_t* counts, int reverse) {
     const uint32_t target = a->pc_target ? a->pc_target : a->per_batch;
     int64_t W = 0;
     for (size_t i = 0; i < bank->n; ++i) W += llrint(bank->v[i].w * 4294967296.0);
@@ -207,10 +209,12 @@ static void cz_control(const or_lcg* l, const or_azurv1_problem* a, uint32_t p, 
             cz_push(next, cp);
         }
     }
+    return w_new;
 }
 
 int or_azurv1_census_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g_begin, uint64_t g_end,
-                         uint64_t event_cap, int64_t* tally, uint64_t* counts, int reverse, uint64_t* pop) {
+                         uint64_t event_cap, int64_t* tally, uint64_t* counts, int reverse, uint64_t* pop,
+                         double* wphase) {
     const uint64_t P = a->per_batch;
     if (a->seeding == OR_SEED_STRIDE || a->n_census < 2 || g_begin % P != 0 || g_end % P != 0) return -1;
     const uint32_t C = a->n_census;
@@ -226,8 +230,10 @@ int or_azurv1_census_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g
             cz_push(&cur, s);
             counts[OR_C_SOURCE]++;
         }
+        double w_phase = 1.0;
         for (uint32_t p = 1; p <= C; ++p) {
             if (pop) pop[(grp - g_begin / P) * C + (p - 1)] = cur.n;
+            if (wphase) wphase[(grp - g_begin / P) * C + (p - 1)] = w_phase;
             const double t0 = cz_census_time(a, p - 1);
             bank.n = 0;
             for (size_t q = 0; q < cur.n; ++q) {
@@ -235,7 +241,7 @@ int or_azurv1_census_run(const or_lcg* l, const or_azurv1_problem* a, uint64_t g
                 status |= cz_follow(l, a, e, t0, p, event_cap, row, counts, &bank, &stk, &stk_cap);
             }
             cur.n = 0;
-            if (p < C) cz_control(l, a, p, &bank, &cur, counts, reverse);
+            if (p < C) w_phase = cz_control(l, a, p, &bank, &cur, counts, reverse);
         }
     }
     free(stk);
