@@ -278,6 +278,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import shard
     from paper_2403_06362_gb300 import workloads as W
 
     ctx = mc.Context(local)
@@ -285,7 +286,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     n = N_STREAMS
-    id0 = rank * n
+    id0, _ = shard.weak_range(rank, n)  # this rank's block of stream ids
     specs = [mc.mc_seed_spec(mode=mc.MC_SEED_HASH, seed=W.HASH_SEED),
              mc.mc_seed_spec(mode=mc.MC_SEED_STRIDE, seed=W.STRIDE_X0, stride_q=W.STRIDE_Q)]
     st = [torch.empty(n, dtype=torch.int64, device=dev) for _ in specs]

@@ -2,7 +2,8 @@
 range, with no exchange on the data path); the ranks' int64 tallies and
 counters summed with an all-reduce are bit-identical to one rank running
 every history.  Checked with two gloo ranks on the CPU, the oracle standing
-in for each rank's device work."""
+in for each rank's device work, on the id ranges the product's sharding
+helper (paper_2403_06362_gb300.shard, which bench.py uses) assigns."""
 import os
 import socket
 
@@ -11,6 +12,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as tmp
 
+from paper_2403_06362_gb300 import shard
 from paper_2403_06362_gb300 import workloads as W
 
 
@@ -32,19 +34,28 @@ def _rank_main(rank, world, port, q):
         L = O.Lcg(m=63, pad=0, g=W.LCG_G, c=1)
         if geom == "slab":
             p = W.slab_small(W.SEED_STRIDE, n_histories=4000)[0]
-            n = p["n_histories"]
-            lo, hi = rank * n // world, (rank + 1) * n // world
+            lo, hi = shard.rank_range(rank, world, p["n_histories"])
             r = O.slab_run(L, W.to_oracle_problem(p, O), lo, hi)
         else:
             b = W.box_problem(n_histories=1500, mesh=8)
-            n = b["n_histories"]
-            lo, hi = rank * n // world, (rank + 1) * n // world
+            lo, hi = shard.rank_range(rank, world, b["n_histories"])
             r = O.box_run(L, W.to_oracle_box(b, O), lo, hi)
         t = torch.from_numpy(r["tally"].copy())
         c = torch.from_numpy(r["counts"][:13].astype(np.int64))
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         dist.all_reduce(c, op=dist.ReduceOp.SUM)
         out[geom] = (t.numpy(), c.numpy())
+    # the microbenchmark's weak-scaling blocks: the ranks' streams are the
+    # consecutive blocks of one rank's double-size run
+    lo, hi = shard.weak_range(rank, 512)
+    st = O.seed_hash(63, W.HASH_SEED, lo, hi - lo)
+    fs, _, dg = O.lcg_draw(63, W.LCG_G, W.LCG_C, st, 8)
+    parts = [torch.zeros(2 * 512, dtype=torch.int64) for _ in range(2)]
+    parts[0][lo:hi] = torch.from_numpy(fs.view(np.int64))
+    parts[1][lo:hi] = torch.from_numpy(dg.view(np.int64))
+    for x in parts:
+        dist.all_reduce(x, op=dist.ReduceOp.SUM)
+    out["streams"] = (parts[0].numpy().view(np.uint64), parts[1].numpy().view(np.uint64))
     if rank == 0:
         q.put(out)
     dist.barrier()
@@ -69,3 +80,15 @@ def test_two_gloo_ranks_sum_to_the_single_rank_result(oracle):
     wb = oracle.box_run(L, W.to_oracle_box(W.box_problem(n_histories=1500, mesh=8), oracle))
     assert np.array_equal(got["box"][0], wb["tally"])
     assert np.array_equal(got["box"][1], wb["counts"][:13].astype(np.int64))
+    st, _, dg = oracle.lcg_draw(63, W.LCG_G, W.LCG_C, oracle.seed_hash(63, W.HASH_SEED, 0, 1024), 8)
+    assert np.array_equal(got["streams"][0], st) and np.array_equal(got["streams"][1], dg)
+
+
+def test_rank_ranges_tile_the_ids():
+    for world in (1, 2, 3, 8):
+        for total in (0, 1, 7, 4000, 10**8 + 3):
+            r = [shard.rank_range(k, world, total) for k in range(world)]
+            assert r[0][0] == 0 and r[-1][1] == total
+            assert all(r[k][1] == r[k + 1][0] for k in range(world - 1))
+            assert max(b - a for a, b in r) - min(b - a for a, b in r) <= 1
+    assert shard.weak_range(3, 2**26) == (3 * 2**26, 4 * 2**26)
