@@ -83,11 +83,20 @@ constexpr size_t kScratchBytes = 256;
 
 // Slab records are followed, 256-byte aligned, by every problem's bin edge
 // and width tables (filled on the device by slab_prep).
+// The tables are followed, 256-byte aligned, by the processing order of a
+// launch of several problems (also filled by slab_prep).
 size_t slab_tables_offset(uint32_t n) { return ((size_t)n * mci::slab_dev_size() + 255u) & ~(size_t)255u; }
+size_t slab_order_offset(const mc_problem* problems, uint32_t n) {
+  return (slab_tables_offset(n) + (size_t)mci::slab_table_doubles(problems, n) * sizeof(double) + 255u) &
+         ~(size_t)255u;
+}
 size_t slab_stage_bytes(const mc_problem* problems, uint32_t n) {
-  return slab_tables_offset(n) + (size_t)mci::slab_table_doubles(problems, n) * sizeof(double);
+  return slab_order_offset(problems, n) + mci::slab_order_bytes(n);
 }
 void* slab_tables_of(mc_ctx* ctx, uint32_t n) { return static_cast<char*>(ctx->problems.ptr) + slab_tables_offset(n); }
+void* slab_order_of(mc_ctx* ctx, const mc_problem* problems, uint32_t n) {
+  return static_cast<char*>(ctx->problems.ptr) + slab_order_offset(problems, n);
+}
 
 // Host half of staging: waits until the pinned buffer is free, sizes the
 // buffers and writes the problem records into pinned memory.
@@ -154,7 +163,8 @@ int stage_problems(mc_ctx* ctx, const mc_problem* problems, uint32_t n, cudaStre
   MC_TRY_CUDA(cudaEventRecord(*ev, s));
   st = pulse ? mci::pulse_prep(ctx->problems.ptr, s)
              : (box ? mci::box_prep(ctx->problems.ptr, n, s)
-                    : mci::slab_prep(ctx->problems.ptr, n, s, slab_tables_of(ctx, n)));
+                    : mci::slab_prep(ctx->problems.ptr, n, s, slab_tables_of(ctx, n),
+                                     slab_order_of(ctx, problems, n)));
   if (st != MC_OK) return st;
   ctx->staged_image->swap(img);
   ctx->staged_kind = kind;
@@ -476,6 +486,12 @@ int validate_run(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uin
   return MC_OK;
 }
 
+uint64_t total_histories(const mc_problem* p, uint32_t n) {
+  uint64_t t = 0;
+  for (uint32_t i = 0; i < n; ++i) t += p[i].n_histories;
+  return t;
+}
+
 int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, uint32_t n_problems,
                      const mc_run_config* cfg, const mc_tally* tally, uint64_t rb, uint64_t re,
                      unsigned long long* ticket, mci::SlabLaunch* out) {
@@ -484,6 +500,10 @@ int make_slab_launch(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems,
   L.d_probs = ctx->problems.ptr;
   L.d_tables = slab_tables_of(ctx, n_problems);
   L.n_problems = n_problems;
+  // A launch of all the histories of 2..kMaxOrderedProblems problems takes
+  // them in the order the prep kernel ranked (longest expected chains first).
+  if (n_problems >= 2 && n_problems <= mci::kMaxOrderedProblems && rb == 0 && re == total_histories(problems, n_problems))
+    mci::slab_order_ptrs(slab_order_of(ctx, problems, n_problems), n_problems, &L.d_order, &L.d_order_begin);
   L.chunk = cfg->chunk ? cfg->chunk : mci::slab_default_chunk(re - rb, ctx->num_sms);
   L.range_begin = rb;
   L.total = re - rb;
@@ -545,7 +565,8 @@ int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, u
     cudaGraph_t g = nullptr;
     MC_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
     cudaMemcpyAsync(ctx->problems.ptr, ctx->h_problems, bytes, cudaMemcpyHostToDevice, cs);
-    mci::slab_prep(ctx->problems.ptr, n_problems, cs, slab_tables_of(ctx, n_problems));
+    mci::slab_prep(ctx->problems.ptr, n_problems, cs, slab_tables_of(ctx, n_problems),
+                   slab_order_of(ctx, problems, n_problems));
     if (!cfg->accumulate) {
       cudaMemsetAsync(tally->d_bins, 0, tally->n_slots * sizeof(int64_t), cs);
       cudaMemsetAsync(tally->d_counts, 0, (size_t)n_problems * MC_NCOUNT * sizeof(uint64_t), cs);

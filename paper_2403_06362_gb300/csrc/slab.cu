@@ -40,7 +40,21 @@ __global__ void slab_tables_kernel(const SlabDev* __restrict__ p, uint32_t n, do
   }
 }
 
-__global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
+// Expected flights per history of a slab problem with a uniform isotropic
+// source, a ranking key only: the first-flight escape probability of such a
+// source in a slab of optical thickness tau is (1 - 2 E3(tau)) / (2 tau)
+// (E3 approximated by exp(-tau) / (tau + 2)), every later flight is taken to
+// escape as often, and a collision continues with probability c:
+// 1 / (1 - c (1 - P_esc)).
+__device__ __forceinline__ float expected_flights(const SlabDev& q) {
+  const float tau = fmaxf((float)(q.L * q.sigma_t), 1e-6f);
+  const float e3 = __expf(-tau) / (tau + 2.0f);
+  const float p_esc = fminf(1.0f, (1.0f - 2.0f * e3) / (2.0f * tau));
+  return 1.0f / fmaxf(1e-6f, 1.0f - (float)q.c * (1.0f - p_esc));
+}
+
+__global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n, uint32_t* __restrict__ order,
+                                 uint64_t* __restrict__ order_begin) {
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     SlabDev& q = p[i];
     q.h = q.L / (double)q.n_bins;
@@ -65,6 +79,26 @@ __global__ void slab_prep_kernel(SlabDev* __restrict__ p, uint32_t n) {
       acc += p[i].n_hist;
     }
   }
+  if (!order) return;
+  // rank by expected flights, descending; ties by index (a stable order)
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float fi = expected_flights(p[i]);
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+      const float fj = expected_flights(p[j]);
+      r += (fj > fi || (fj == fi && j < i)) ? 1u : 0u;
+    }
+    order[r] = i;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t acc = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+      order_begin[k] = acc;
+      acc += p[order[k]].n_hist;
+    }
+    order_begin[n] = acc;
+  }
 }
 
 struct RunArgs {
@@ -85,6 +119,7 @@ struct RunArgs {
   uint32_t donate_max;  // a warp with 1..donate_max live lanes after the ticket ran out donates them
   uint32_t pool_cap;    // particles the block's shared pool holds (0: no compaction)
   uint32_t lock_attempts;  // attempts at the pool lock before a warp gives up
+  mcs::Order order;        // processing order of several problems (empty: id order)
 };
 
 // In-block compaction of the long-chain tail.  Once the ticket runs out,
@@ -146,15 +181,6 @@ __device__ __forceinline__ uint32_t pool_get(const unsigned long long* e, mcs::R
   events = e[8];
   q.xlo = __uint_as_float((uint32_t)e[9]);
   return (uint32_t)(e[6] >> 32);
-}
-
-__device__ __forceinline__ uint32_t find_problem(const SlabDev* p, uint32_t n, uint64_t gi) {
-  uint32_t lo = 0, hi = n - 1;  // largest i with hist_begin <= gi
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (p[mid].hist_begin <= gi) lo = mid; else hi = mid - 1;
-  }
-  return lo;
 }
 
 template <int M, bool F32, bool SMEM, bool AGG>
@@ -222,8 +248,8 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
       const uint64_t avail = pool_end - pool_next;
       const unsigned rank = __popc(dead & lt_mask);
       if (!alive && rank < avail) {
-        gi = a.range_begin + pool_next + rank;
-        const uint32_t pi = a.nprob == 1 ? 0u : find_problem(a.probs, a.nprob, gi);
+        uint32_t pi;
+        mcs::ticket_history(a.probs, a.nprob, a.range_begin, a.order, pool_next + rank, pi, gi);
         if ((int)pi != lc.prob) { lc.flush(a.counts); lc.prob = (int)pi; }
         P = a.probs + pi;
         const uint64_t id = gi - P->hist_begin;
@@ -445,8 +471,10 @@ void slab_fill_host(const mc_problem* src, uint32_t n, void* dst) {
   }
 }
 
-int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables) {
-  slab_prep_kernel<<<1, 256, 0, s>>>(static_cast<SlabDev*>(d_probs), n);
+int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables, void* d_order) {
+  uint32_t* order = d_order && n >= 2 && n <= kMaxOrderedProblems ? static_cast<uint32_t*>(d_order) : nullptr;
+  uint64_t* begin = order ? reinterpret_cast<uint64_t*>(order + ((n + 1u) & ~1u)) : nullptr;
+  slab_prep_kernel<<<1, 256, 0, s>>>(static_cast<SlabDev*>(d_probs), n, order, begin);
   int st = cuda_status(cudaGetLastError(), "slab_prep_kernel launch");
   if (st != MC_OK || !d_tables) return st;
   slab_tables_kernel<<<std::min<uint32_t>(n, 1024u), 64, 0, s>>>(static_cast<const SlabDev*>(d_probs), n,
@@ -488,6 +516,7 @@ int slab_history_launch(const SlabLaunch& L, cudaStream_t s) {
   a.donate_max = 12;
   a.pool_cap = L.block >= 64 ? (uint32_t)((L.block >> 5) - 1) * a.donate_max : 0u;
   a.lock_attempts = L.pool_lock_attempts;
+  a.order = mcs::Order{L.d_order, L.d_order_begin};
   if (L.tally_agg) {
     if (L.lcg.m == 63) return launch_history_m<63, true>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);
     return launch_history_m<0, true>(a, L.f32, L.block, L.blocks_per_sm, L.num_sms, s);

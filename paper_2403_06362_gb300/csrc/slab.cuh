@@ -81,6 +81,44 @@ __device__ __forceinline__ uint64_t slab_seed(const SlabDev& p, uint64_t id, con
   return mcd::hash_with(id, p.seed_hash) & mask;
 }
 
+// The processing order of a launch of several problems: problem order[k]'s
+// histories take ticket positions [begin[k], begin[k + 1]) (the prep kernel
+// ranks the problems by their expected flights per history, longest first,
+// so that the long chains start early and do not form the launch's tail).
+// An empty order (order == nullptr) takes the histories in id order from
+// range_begin.  Either way history gi keeps its own stream, so the order
+// changes no result.
+struct Order {
+  const uint32_t* order;
+  const uint64_t* begin;
+};
+
+__device__ __forceinline__ uint32_t find_problem_of(const SlabDev* p, uint32_t n, uint64_t gi) {
+  uint32_t lo = 0, hi = n - 1;  // largest i with hist_begin <= gi
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (p[mid].hist_begin <= gi) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Problem and global history index of ticket position t.
+__device__ __forceinline__ void ticket_history(const SlabDev* p, uint32_t n, uint64_t range_begin, const Order& o,
+                                               uint64_t t, uint32_t& pi, uint64_t& gi) {
+  if (o.order) {
+    uint32_t lo = 0, hi = n - 1;  // largest k with begin[k] <= t
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (o.begin[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    pi = o.order[lo];
+    gi = p[pi].hist_begin + (t - o.begin[lo]);
+    return;
+  }
+  gi = range_begin + t;
+  pi = n == 1 ? 0u : find_problem_of(p, n, gi);
+}
+
 __device__ __forceinline__ uint64_t batch_of(uint64_t id, uint64_t n_hist, uint32_t n_batches) {
   // floor(id * n_batches / n_hist) without 128-bit arithmetic when it fits.
   if (id <= (~0ull) / (n_batches ? n_batches : 1)) return (id * n_batches) / n_hist;

@@ -87,6 +87,7 @@ struct EvArgs {
   uint32_t smem_edges;    // one problem: its n_bins + 1 edges and n_bins widths in shared memory (0: none)
   const double* tables;   // else each problem's edge and width tables in global memory (nullable)
   uint32_t smem_counts;   // 1: 2..kSmemCountProblems problems, counters staged in shared memory
+  mcs::Order order;       // processing order of several problems (empty: id order)
   EvBank<F32> b;
 };
 
@@ -198,20 +199,12 @@ __device__ __forceinline__ unsigned long long take_history(unsigned long long* t
   return base + rank;
 }
 
-__device__ __forceinline__ uint32_t find_problem_ev(const SlabDev* p, uint32_t n, uint64_t gi) {
-  uint32_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (p[mid].hist_begin <= gi) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Starts history t (relative to range_begin) in `v`.
+// Starts the history at ticket position t in `v`.
 template <int M, bool F32>
 __device__ __forceinline__ void start_history(const EvArgs<F32>& a, const mcd::Affine* tab, uint64_t t, EvLive& v) {
-  const uint64_t gi = a.range_begin + t;
-  const uint32_t pi = a.nprob == 1 ? 0u : find_problem_ev(a.probs, a.nprob, gi);
+  uint32_t pi;
+  uint64_t gi;
+  mcs::ticket_history(a.probs, a.nprob, a.range_begin, a.order, t, pi, gi);
   const SlabDev& P = a.probs[pi];
   const uint64_t id = gi - P.hist_begin;
   mcs::Rng<M> r{mcs::slab_seed(P, id, tab, a.lcg.mask), 0ull};
@@ -557,6 +550,7 @@ int slab_event_run_t(const mci::SlabLaunch& L, void* d_bank, uint32_t cap, unsig
   a.smem_edges = (L.n_problems == 1 && L.single_n_bins + 1 <= 4096) ? L.single_n_bins + 1 : 0u;
   a.tables = a.smem_edges ? nullptr : static_cast<const double*>(L.d_tables);
   a.smem_counts = (L.n_problems > 1 && L.n_problems <= kSmemCountProblems) ? 1u : 0u;
+  a.order = mcs::Order{L.d_order, L.d_order_begin};
   const size_t smem = a.smem_edges ? (size_t)a.smem_edges * 16u
                                    : (a.smem_counts ? (size_t)L.n_problems * MC_NCOUNT * 8u : 0u);
   carve<F32>(d_bank, cap, &a.b);

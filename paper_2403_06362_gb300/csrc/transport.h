@@ -25,6 +25,9 @@ struct SlabLaunch {
   bool f32;
   int block, blocks_per_sm, num_sms;
   uint32_t pool_lock_attempts = 1u << 20;  // compaction-pool lock (mc_limits)
+  // processing order of several problems (slab_prep's d_order area; null: id order)
+  const uint32_t* d_order = nullptr;
+  const uint64_t* d_order_begin = nullptr;
   bool tally_agg = true;                   // warp-aggregated tally atomics
   uint64_t event_iterations = ~0ull;       // event schedule bound (mc_limits; ~0: derived)
 };
@@ -32,8 +35,16 @@ struct SlabLaunch {
 size_t slab_dev_size();
 void slab_fill_host(const mc_problem* src, uint32_t n, void* dst);
 // d_tables (nullable): room for slab_table_doubles(...) doubles, filled
-// with every problem's bin edges and widths.
-int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables = nullptr);
+// with every problem's bin edges and widths.  d_order (nullable):
+// slab_order_bytes(n) bytes, filled for 2..kMaxOrderedProblems problems with
+// their processing order (slab_order_ptrs gives the two arrays).
+constexpr uint32_t kMaxOrderedProblems = 4096;
+int slab_prep(void* d_probs, uint32_t n, cudaStream_t s, void* d_tables = nullptr, void* d_order = nullptr);
+inline size_t slab_order_bytes(uint32_t n) { return (size_t)((n + 1u) & ~1u) * 4u + (size_t)(n + 1u) * 8u; }
+inline void slab_order_ptrs(void* d_order, uint32_t n, const uint32_t** order, const uint64_t** begin) {
+  *order = static_cast<const uint32_t*>(d_order);
+  *begin = reinterpret_cast<const uint64_t*>(*order + ((n + 1u) & ~1u));
+}
 uint64_t slab_table_doubles(const mc_problem* src, uint32_t n);
 int slab_history_launch(const SlabLaunch& L, cudaStream_t s);
 
