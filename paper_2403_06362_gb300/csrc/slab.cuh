@@ -240,11 +240,24 @@ __device__ __forceinline__ float slab_edge_f(const SlabDev& p, int j) {
 // displacement is far below an ulp of its position (a direction nearly
 // parallel to the faces, where 1 / |mu| is large) keeps its true length
 // instead of an ulp of the position times 1 / |mu|.
+__device__ __forceinline__ int bin_of_pair(const SlabDev& p, float h, float l) {
+  // the largest j with e_j <= h + l (fp32 edges), from the scaled guess
+  const int nb = (int)p.n_bins;
+  int j = clamp_bin((int)(h * p.inv_h_f), nb);
+  while (j > 0) {
+    const float e = slab_edge_f(p, j);
+    if (h < e || (h == e && l < 0.0f)) --j; else break;
+  }
+  while (j + 1 < nb) {
+    const float e = slab_edge_f(p, j + 1);
+    if (h > e || (h == e && l >= 0.0f)) ++j; else break;
+  }
+  return j;
+}
+
 __device__ __forceinline__ void seg32(const SlabDev& p, float ah, float al, float bh, float bl, float w_mu,
                                       const Sink& s) {
-  const int nb = (int)p.n_bins;
-  const int j0 = clamp_bin((int)(ah * p.inv_h_f) - 1, nb);
-  const int j1 = clamp_bin((int)(bh * p.inv_h_f) + 1, nb);
+  const int j0 = bin_of_pair(p, ah, al), j1 = bin_of_pair(p, bh, bl);
   for (int j = j0; j <= j1; ++j) {
     const float lo_e = slab_edge_f(p, j), hi_e = slab_edge_f(p, j + 1);
     // max(a, lo_e) and min(b, hi_e) as pairs (an edge's low part is zero)
