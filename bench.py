@@ -51,7 +51,6 @@ DRAWS = 64
 # fp64 value; both fractions are printed.
 OPS_PER_DRAW = 11
 OPS_PER_DRAW_KERNEL_FORM = 10
-E2E_SLICES = 16  # id slices per mode in the end-to-end leg
 # DRAM bytes (read + write) per launch of the draw kernel at 2^26 streams, from
 # an ncu capture of the kernel as built (mean of the hash and stride launches;
 # profiles/draw_digest_m63_kernel_rng_microbench.md).
@@ -346,49 +345,34 @@ def main():
                 "ops_per_draw_kernel_form": OPS_PER_DRAW_KERNEL_FORM,
                 "frac_kernel_form": OPS_PER_DRAW_KERNEL_FORM * n * DRAWS / (launch_ms / 1e3) / peak}
 
-    # End to end through the public call: every final state and digest is
-    # copied to pinned host memory inside the timed region, every step.  The
-    # id range of each mode is cut into slices (mc_lcg_draw takes any id
-    # range); a copy stream drains slice j while the launch stream computes
-    # slice j + 1, and a slice is recomputed only after its previous copy has
-    # finished.  The device-to-host link (about 190 GB/s measured on this
-    # machine) bounds the result.
+    # End to end through the public call on host buffers: mc_lcg_draw_host
+    # returns every final state and digest into page-locked host memory
+    # (2 GiB per step), slicing the range internally so that each slice's
+    # device-to-host copy overlaps the next slice's kernel; the call returns
+    # once the results are in host memory.  The device-to-host link (about
+    # 190 GB/s measured on this machine) bounds the result.
     h_st = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
     h_dg = [torch.empty(n, dtype=torch.int64, pin_memory=True) for _ in specs]
     e2e_steps = max(3, min(20, args.steps))
-    sl = n // E2E_SLICES
-    copy_stream = torch.cuda.Stream(device=dev)
-    copied = [[None] * E2E_SLICES for _ in specs]
+    for i in range(2):  # warm-up: the context's device slots and copy stream
+        mc.mc_lcg_draw_host(ctx, lcg, specs[i], id0, h_st[i], n, DRAWS, h_dg[i], stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
     for k in range(e2e_steps):
         for i in range(2):
-            for j in range(E2E_SLICES):
-                lo, hi = j * sl, (j + 1) * sl
-                if copied[i][j] is not None:
-                    stream.wait_event(copied[i][j])
-                mc.mc_lcg_draw(ctx, lcg, specs[i], id0 + lo, st[i][lo:hi], sl, DRAWS, None, dg[i][lo:hi], stream)
-                done = torch.cuda.Event()
-                done.record(stream)
-                copy_stream.wait_event(done)
-                with torch.cuda.stream(copy_stream):
-                    h_st[i][lo:hi].copy_(st[i][lo:hi], non_blocking=True)
-                    h_dg[i][lo:hi].copy_(dg[i][lo:hi], non_blocking=True)
-                    copied[i][j] = torch.cuda.Event()
-                    copied[i][j].record(copy_stream)
-    stream.wait_stream(copy_stream)
-    e1.record(stream)
+            mc.mc_lcg_draw_host(ctx, lcg, specs[i], id0, h_st[i], n, DRAWS, h_dg[i], stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = 1e3 * (time.perf_counter() - t0) / e2e_steps
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e = {"value": draws_per_step / (e2e_ms / 1e3), "unit": "draws/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": 2 * 2 * n * 8,
-           "note": "inputs are scalars (seed, id range); every final state and digest is copied to host, "
-                   f"in {E2E_SLICES} id slices per mode overlapped with the draw kernels"}
+           "note": "one mc_lcg_draw_host call per mode on page-locked host buffers, host clock around the calls; "
+                   "inputs are scalars (seed, id range); every final state and digest reaches host memory"}
 
     detail = {"draws_per_s_hash": n * DRAWS * world / (statistics.mean(t_hash) / 1e3),
               "draws_per_s_stride": n * DRAWS * world / (statistics.mean(t_str) / 1e3),

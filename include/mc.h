@@ -162,6 +162,25 @@ MC_API int mc_lcg_draw(mc_ctx* ctx, const mc_lcg* lcg, const mc_seed_spec* seed,
                        uint64_t* d_states, uint64_t n_streams, uint32_t draws, double* d_u,
                        uint64_t* d_digest, void* stream);
 
+/* mc_lcg_draw on HOST buffers (Section 2, Eq. 1; seeds by Eqs. 2-4): the
+ * same streams, draws, final states and digests, for a caller that holds
+ * its inputs and wants its results in host memory.
+ *   seed      as for mc_lcg_draw; NULL: h_states holds the input states.
+ *   h_states  nullable with a seed (then no final states are returned);
+ *             host uint64_t[n_streams], in/out without a seed.
+ *   h_digest  nullable host uint64_t[n_streams].  At least one of h_states
+ *             and h_digest is required.
+ * The range is processed in slices of 2^22 streams through two device slots
+ * owned by the context (128 MiB, allocated on the first call): the draw
+ * kernel of one slice runs on `stream` while a private copy stream returns
+ * the previous slice.  Page-locked host buffers (cudaHostAlloc) let the
+ * copies overlap the kernels; pageable ones work, serialised.  The call
+ * returns when every result is in host memory.  Not for use inside stream
+ * capture.  Errors: as mc_lcg_draw, MC_ERR_ARG without an output. */
+MC_API int mc_lcg_draw_host(mc_ctx* ctx, const mc_lcg* lcg, const mc_seed_spec* seed, uint64_t id_begin,
+                            uint64_t* h_states, uint64_t n_streams, uint32_t draws, uint64_t* h_digest,
+                            void* stream);
+
 /* --------------------------------------------------------------- transport
  * History-based (or event-based) one-speed transport in a slab, or
  * multigroup transport in a two-region box; every source history owns one

@@ -155,6 +155,27 @@ def mc_lcg_draw(ctx, lcg, seed, id_begin, d_states, n_streams, draws, d_u=None, 
                                       n_streams, draws, _ptr(d_u), _ptr(d_digest), _stream(stream)))
 
 
+def _host_ptr(a) -> Optional[int]:
+    """Raw pointer of a host buffer: a torch CPU tensor or a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("mc_lcg_draw_host needs contiguous host buffers")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("mc_lcg_draw_host needs contiguous host buffers")
+    return a.ctypes.data
+
+
+def mc_lcg_draw_host(ctx, lcg, seed, id_begin, h_states, n_streams, draws, h_digest=None, stream=None):
+    """mc_lcg_draw on host buffers (uint64 / int64 arrays or CPU tensors;
+    page-locked ones let the library overlap copies and kernels)."""
+    sp = C.byref(seed) if seed is not None else None
+    return _ffi.check(lib().mc_lcg_draw_host(ctx.handle, C.byref(lcg), sp, id_begin, _host_ptr(h_states),
+                                           n_streams, draws, _host_ptr(h_digest), _stream(stream)))
+
+
 def problem_array(problems: Sequence[mc_problem]):
     arr = (mc_problem * len(problems))(*problems)
     return arr

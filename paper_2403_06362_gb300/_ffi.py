@@ -34,7 +34,7 @@ EXPORTED = [
     "mc_lcg_draw", "mc_transport_run", "mc_tally_read", "mc_hash64", "mc_normality",
     "mc_transport_run_static", "mc_autotune", "mc_log1m", "mc_log1m_device", "mc_recip_rn",
     "mc_two_u_minus_1", "mc_recip_rn_device", "mc_llrint_nonneg", "mc_d_lt", "mc_mul_small",
-    "mc_ctx_set_limits", "mc_ctx_get_limits",
+    "mc_ctx_set_limits", "mc_ctx_get_limits", "mc_lcg_draw_host",
 ]
 
 
@@ -127,6 +127,7 @@ def _load():
         "mc_seed_hash": (i32, [P, C.POINTER(mc_lcg), u64, u64, u64, P, P]),
         "mc_seed_stride": (i32, [P, C.POINTER(mc_lcg), u64, u64, u64, u64, P, P]),
         "mc_lcg_draw": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_seed_spec), u64, P, u64, u32, P, P, P]),
+        "mc_lcg_draw_host": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_seed_spec), u64, P, u64, u32, P, P]),
         "mc_transport_run": (i32, [P, C.POINTER(mc_lcg), C.POINTER(mc_problem), u32,
                                    C.POINTER(mc_run_config), C.POINTER(mc_tally), P]),
         "mc_tally_read": (i32, [P, C.POINTER(mc_problem), u32, C.POINTER(mc_tally), P, P, P, P, P, P]),

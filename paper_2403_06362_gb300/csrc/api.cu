@@ -450,6 +450,12 @@ MC_API void mc_ctx_destroy(mc_ctx* ctx) {
     delete ctx->graphs;
   }
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  ctx->host_io.release();
+  if (ctx->io_stream) cudaStreamDestroy(ctx->io_stream);
+  for (int k = 0; k < 2; ++k) {
+    if (ctx->io_computed[k]) cudaEventDestroy(ctx->io_computed[k]);
+    if (ctx->io_copied[k]) cudaEventDestroy(ctx->io_copied[k]);
+  }
   delete ctx;
 }
 

@@ -116,6 +116,12 @@ struct mc_ctx {
   // the legacy default stream, which cannot be captured).
   cudaStream_t capture_stream = nullptr;
   mci::GraphCache* graphs = nullptr;
+  // mc_lcg_draw_host: two device slots of a slice's states and digests, a
+  // copy stream and the events that order the slots' reuse.
+  mci::DeviceBuf host_io;
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_computed[2] = {nullptr, nullptr};
+  cudaEvent_t io_copied[2] = {nullptr, nullptr};
   // Autotuner: scratch tally and the best configuration per workload shape.
   mci::DeviceBuf tune_tally;
   std::unordered_map<uint64_t, mc_run_config>* tune_cache = nullptr;

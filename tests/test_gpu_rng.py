@@ -217,3 +217,52 @@ def test_digest_kernel_long_streams(env, oracle):
     o_st, _, o_dg = oracle.lcg_draw(M, G, CC, seeds, draws, want_u=False)
     assert np.array_equal(u64(v), o_st)
     assert np.array_equal(u64(dg), o_dg)
+
+
+@pytest.mark.parametrize("mode", ["hash", "stride"])
+def test_draw_host_buffers_match_the_device_call(env, oracle, mode):
+    """mc_lcg_draw_host (host buffers, two device slots, a copy stream)
+    returns the device call's final states and digests bit for bit over a
+    range of several 2^22-stream slices with a ragged end, into page-locked
+    tensors and into plain numpy arrays; sampled streams equal the oracle."""
+    mc, ctx, torch = env
+    n, id0, draws = 2 * 2**22 + 12_345, 77, 64
+    spec = (mc.mc_seed_spec(mode=mc.MC_SEED_HASH, seed=W.HASH_SEED) if mode == "hash"
+            else mc.mc_seed_spec(mode=mc.MC_SEED_STRIDE, seed=W.STRIDE_X0, stride_q=Q))
+    d_st = torch.empty(n, dtype=torch.int64, device="cuda")
+    d_dg = torch.empty(n, dtype=torch.int64, device="cuda")
+    mc.mc_lcg_draw(ctx, mc.make_lcg(), spec, id0, d_st, n, draws, None, d_dg)
+    ref_st, ref_dg = u64(d_st), u64(d_dg)
+    h_st = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    h_dg = torch.empty(n, dtype=torch.int64, pin_memory=True)
+    mc.mc_lcg_draw_host(ctx, mc.make_lcg(), spec, id0, h_st, n, draws, h_dg)
+    assert np.array_equal(h_st.numpy().view(np.uint64), ref_st)
+    assert np.array_equal(h_dg.numpy().view(np.uint64), ref_dg)
+    a_dg = np.zeros(n, dtype=np.uint64)  # pageable, digests only
+    mc.mc_lcg_draw_host(ctx, mc.make_lcg(), spec, id0, None, n, draws, a_dg)
+    assert np.array_equal(a_dg, ref_dg)
+    idx = np.random.default_rng(5).integers(0, n, 64)
+    for i in idx:
+        k = id0 + int(i)
+        s0 = (oracle.seed_hash(M, W.HASH_SEED, k, 1) if mode == "hash"
+              else oracle.seed_stride(M, G, CC, W.STRIDE_X0, Q, k, 1))
+        fs, _, dg = oracle.lcg_draw(M, G, CC, s0, draws, want_u=False)
+        assert int(fs[0]) == int(ref_st[i]) and int(dg[0]) == int(ref_dg[i])
+
+
+def test_draw_host_buffers_without_seed_and_errors(env, oracle):
+    mc, ctx, torch = env
+    n = 2**22 + 5
+    st0 = oracle.seed_hash(M, 42, 0, n)
+    h_st = st0.copy()
+    h_dg = np.zeros(n, dtype=np.uint64)
+    mc.mc_lcg_draw_host(ctx, mc.make_lcg(), None, 0, h_st, n, 9, h_dg)
+    fs, _, dg = oracle.lcg_draw(M, G, CC, st0[:1000], 9, want_u=False)
+    assert np.array_equal(h_st[:1000], fs) and np.array_equal(h_dg[:1000], dg)
+    fs, _, dg = oracle.lcg_draw(M, G, CC, st0[-7:], 9, want_u=False)
+    assert np.array_equal(h_st[-7:], fs) and np.array_equal(h_dg[-7:], dg)
+    with pytest.raises(mc.McError):  # no seed and no states
+        mc.mc_lcg_draw_host(ctx, mc.make_lcg(), None, 0, None, 10, 4, h_dg)
+    spec = mc.mc_seed_spec(mode=mc.MC_SEED_HASH, seed=42)
+    with pytest.raises(mc.McError):  # no output
+        mc.mc_lcg_draw_host(ctx, mc.make_lcg(), spec, 0, None, 10, 4, None)
