@@ -785,20 +785,39 @@ int autotune_impl(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, ui
       have_event = true;
     }
   }
-  // The sample ranks the shapes of one schedule, but the two schedules scale
-  // differently from a sample to the whole (the history schedule's tail is a
-  // larger share of a small run): when the event schedule wins the sample,
-  // the best history shape and it are timed again on the whole range.
-  if (st == MC_OK && have_hist && have_event && S < total && best->schedule == MC_SCHED_EVENT) {
-    mc_run_config rh = best_hist, re = event;
-    rh.range_begin = re.range_begin = 0;
-    rh.range_end = re.range_end = total;
-    float th = 0.0f, te = 0.0f;
-    st = time_run(rh, &th);
-    if (st == MC_OK) st = time_run(re, &te);
+  // A sample ranks shapes as they behave on a quarter of the histories, not
+  // on the whole: the history schedule's tail is a larger share of a small
+  // run, and a chunk that balances a quarter can be too fine or too coarse
+  // for the whole (256 batched problems: chunks of 1/4 or 4 times the
+  // default take 45-50 ms against 20 ms).  So, whenever the sample is not
+  // the whole range, the sample's winner, the best history shape and the
+  // library's default shape are timed again on the whole range and the
+  // fastest of them is kept.
+  if (st == MC_OK && have && S < total) {
+    mc_run_config dflt = *base;
+    dflt.schedule = MC_SCHED_HISTORY;
+    dflt.block = 0;
+    dflt.chunk = 0;
+    dflt.use_graph = 0;
+    dflt.accumulate = 0;
+    std::vector<mc_run_config> finals{*best, dflt};
+    if (have_hist) finals.push_back(best_hist);
+    float best_full = 0.0f;
+    mc_run_config pick = *best;
+    for (size_t i = 0; i < finals.size() && st == MC_OK; ++i) {
+      mc_run_config r = finals[i];
+      r.range_begin = 0;
+      r.range_end = total;
+      float ms = 0.0f;
+      st = time_run(r, &ms);
+      if (st == MC_OK && (i == 0 || ms < best_full)) {
+        best_full = ms;
+        pick = finals[i];
+      }
+    }
     if (st == MC_OK) {
-      *best = th <= te ? best_hist : event;
-      best_t = th <= te ? th : te;
+      *best = pick;
+      best_t = best_full;
     }
   }
   cudaEventDestroy(e0);

@@ -372,7 +372,10 @@ def test_autotune_leaves_tally_alone_and_auto_matches(env):
     best, ms = mc.mc_autotune(ctx, mc.make_lcg(), cprobs, mc.mc_run_config(), tally.c)
     torch.cuda.synchronize()
     assert int(tally.bins.min()) == 12345 and int(tally.bins.max()) == 12345
-    assert ms > 0 and best.schedule in (0, 1) and best.block in (128, 256, 512)
+    # block 0 with chunk 0: the library's default shape, which the full-range
+    # check keeps when no sampled shape beats it on the whole range
+    assert ms > 0 and best.schedule in (0, 1) and best.block in (0, 128, 256, 512)
+    assert (best.block == 0) == (best.chunk == 0)
     ref, _ = gpu_run(env, probs, n_hist_out=False)
     auto, _ = gpu_run(env, probs, n_hist_out=False, schedule=2)
     again, _ = gpu_run(env, probs, n_hist_out=False, schedule=2)
