@@ -119,6 +119,7 @@ struct RunArgs {
   uint32_t donate_max;  // a warp with 1..donate_max live lanes after the ticket ran out donates them
   uint32_t pool_cap;    // particles the block's shared pool holds (0: no compaction)
   uint32_t lock_attempts;  // attempts at the pool lock before a warp gives up
+  uint32_t coop_slots;     // event records of the cooperative tail the pool's memory holds
   mcs::Order order;        // processing order of several problems (empty: id order)
 };
 
@@ -183,6 +184,352 @@ __device__ __forceinline__ uint32_t pool_get(const unsigned long long* e, mcs::R
   return (uint32_t)(e[6] >> 32);
 }
 
+// What the end of a history and the cooperative tail need of the launch.
+struct TailArgs {
+  uint64_t* hist_state;
+  uint64_t* hist_draws;
+  unsigned long long* counts;
+  mcd::Lcg lcg;
+  uint64_t event_cap;
+};
+
+// The cooperative tail's view of the launch: the tail's own fields and what
+// it needs to rebuild a history's tally sink.
+struct CoopArgs {
+  TailArgs t;
+  const SlabDev* probs;
+  unsigned long long* tally;  // the block's staged tally or the global one
+  const double* tables;       // per-problem edge and width tables (nullable)
+  const double* edges;        // single problem: edges and widths in shared memory (nullable)
+  const double* widths;
+  bool agg;
+};
+
+// End of a history: its draws into the lane's counters, its final state and
+// draw count where the caller asked for them.
+template <int M>
+__device__ __forceinline__ void end_history(const TailArgs& t, const mcs::Rng<M>& r, const SlabDev* P, uint64_t gi,
+                                            mcs::LaneCounts& lc) {
+  lc.draws += r.draws;
+  if (r.draws > lc.maxd) lc.maxd = r.draws;
+  if (P->stride_q != 0 && r.draws > P->stride_q) { ++lc.exh; lc.exd += r.draws - P->stride_q; }
+  if (t.hist_state) t.hist_state[gi] = r.x & t.lcg.mask;
+  if (t.hist_draws) t.hist_draws[gi] = r.draws;
+  if (lc.draws > (1ull << 31)) lc.flush(t.counts);
+}
+
+// Cooperative tail.  When the ticket has run out, the block's pool is empty
+// and its last warp holds at most kCoopMax live histories, the rest of the
+// launch is the latency of those few chains: one lane runs each, and a
+// flight's dependent instructions (the logarithm of its uniform, its product
+// with the direction, the absorption test, the next direction and its
+// reciprocal) leave the other lanes idle.  But a history's draws have fixed
+// roles -- each event takes one draw for the distance, one for the
+// absorption test and one for the new direction, until the history ends --
+// so everything that depends on the draws alone can be computed ahead.  The
+// warp splits into one group of 32 / kp lanes per live history (kp: the live
+// count rounded up to a power of two) and advances every history by rounds
+// of E events:
+//   1. the group's lanes compute, for each event e of the round, the
+//      distance d_e, the product p_e = d_e mu_e, the absorption test and the
+//      direction mu_{e+1} with its tally weight, jumping the stream to draw
+//      3e with the maps of 2^j steps;
+//   2. the history's own lane runs the chain of positions alone, x_{e+1} =
+//      x_e + p_e and the face tests, until the round ends or the history
+//      does (an event cap, a leak, an absorption);
+//   3. the group's lanes make the tally contributions of the round's events.
+// Every value comes from the same function, with the same operands, as in
+// the one-lane path, so the draws, tallies and counters are the same bits.
+// The round's event records sit in the (then empty) pool's shared memory.
+// The warp's histories and the launch's arguments come in through shared
+// memory, and the function, kept out of line, runs the histories to their
+// ends and flushes the lanes' counters: the main loop ends first, and no
+// register of it stays live across the call.
+constexpr int kCoopMax = 4;        // live histories at most
+constexpr int kCoopWords = 6;      // 8-byte words per event record
+constexpr uint32_t kCoopEvents = 128;  // events per history and round at most
+constexpr uint32_t kCoopMinEvents = 8;
+
+__device__ __forceinline__ int coop_groups(int nlive) { return nlive <= 1 ? 1 : nlive <= 2 ? 2 : nlive <= 4 ? 4 : 8; }
+
+__device__ __forceinline__ uint32_t coop_events(uint32_t slots, int kp) {
+  const uint32_t per = slots / (uint32_t)kp;  // records per history: E events and the direction after them
+  return per > 1u ? min(kCoopEvents, per - 1u) : 0u;
+}
+
+__device__ __forceinline__ mcd::Affine affine_steps(const mcd::Affine* tab, uint64_t k) {
+  mcd::Affine acc{1ull, 0ull};
+  while (k) {
+    const int j = __ffsll((long long)k) - 1;
+    acc = mcd::compose(tab[j], acc);
+    k &= k - 1;
+  }
+  return acc;
+}
+
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  return ((unsigned long long)__float_as_uint(b) << 32) | __float_as_uint(a);
+}
+__device__ __forceinline__ float lo_of(unsigned long long w) { return __uint_as_float((uint32_t)w); }
+__device__ __forceinline__ float hi_of(unsigned long long w) { return __uint_as_float((uint32_t)(w >> 32)); }
+__device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ double dval(unsigned long long w) { return __longlong_as_double((long long)w); }
+
+// The records of one history's round, six arrays of E + 1 words.
+struct CoopRec {
+  unsigned long long* p;  // p_e = d_e mu_e (fp32: pr and pe, the product and its error)
+  unsigned long long* d;  // d_e (fp32: d_e and muf_e)
+  unsigned long long* m;  // mu_e (fp32: the state of event e's distance draw)
+  unsigned long long* w;  // tally weight of event e's flight
+  unsigned long long* x;  // position at the start of event e
+  unsigned long long* f;  // absorption test of event e
+  __device__ __forceinline__ CoopRec(unsigned long long* r, uint32_t E)
+      : p(r), d(r + (E + 1u)), m(r + 2u * (E + 1u)), w(r + 3u * (E + 1u)), x(r + 4u * (E + 1u)),
+        f(r + 5u * (E + 1u)) {}
+};
+
+// Phase 1 of a round of the cooperative tail, on lane hl of the G lanes of
+// a history's group: the draw-only values of the events e = hl, hl + G, ...
+// (out of line: the logarithm and the reciprocal keep their registers to
+// themselves).
+template <int M, bool F32>
+__device__ __noinline__ void coop_draws(const mcd::Affine* tab, const SlabDev* pp, mcd::Lcg l, uint64_t x0,
+                                        uint32_t rec_off, uint32_t E, int G, int hl, double mu0, double w0,
+                                        float muf0, float wf0) {
+  extern __shared__ unsigned long long s_dyn[];
+  const CoopRec R(s_dyn + rec_off, E);
+  const SlabDev& p = *pp;
+  const mcd::Affine step3g = affine_steps(tab, 3ull * (uint64_t)G);
+  uint64_t xs = mcs::skip_tab(tab, x0, 3ull * (uint64_t)hl);  // the state after 3e draws
+  for (uint32_t e = (uint32_t)hl; e <= E; e += (uint32_t)G) {
+    if constexpr (!F32) {
+      double mu = mu0, w = w0;
+      if (e != 0u) {
+        mu = mcx::two_u_minus_1(mcd::u53<M>(xs, l.m));
+        w = mcs::fix_per_mu(mu);
+      }
+      R.m[e] = dbits(mu);
+      R.w[e] = dbits(w);
+      if (e < E) {
+        const uint64_t sd = mcd::lcg_step(xs, l.g, l.c);
+        const double d = __dmul_rn(-mclog::log1m_n(mcd::u53<M>(sd, l.m)), p.inv_st);
+        R.d[e] = dbits(d);
+        R.p[e] = dbits(__dmul_rn(d, mu));
+        R.f[e] = mcd::u53<M>(mcd::lcg_step(sd, l.g, l.c), l.m) < p.p_abs_n ? 1ull : 0ull;
+      }
+    } else {
+      float muf = muf0, wf = wf0;
+      if (e != 0u) {
+        muf = mcs::mu_f32(mcd::u53<M>(xs, l.m));
+        wf = muf != 0.0f ? __frcp_rn(fabsf(muf)) : 0.0f;
+      }
+      R.w[e] = pack2(wf, 0.0f);
+      float d = 0.0f;
+      if (e < E) {
+        const uint64_t sd = mcd::lcg_step(xs, l.g, l.c);
+        d = mcs::flight_f32(mcd::u01<M>(sd, l.m)) * p.inv_st_f;
+        const float pr = __fmul_rn(d, muf);
+        R.p[e] = pack2(pr, __fmaf_rn(d, muf, -pr));
+        R.m[e] = sd;
+        R.f[e] = mcd::u53<M>(mcd::lcg_step(sd, l.g, l.c), l.m) < p.p_abs_n ? 1ull : 0ull;
+      }
+      R.d[e] = pack2(d, muf);
+    }
+    xs = mcd::apply(step3g, xs);
+  }
+}
+
+// Phase 3: the tally contributions of the round's events e = hl, hl + G, ...
+// of the nev events the history ran (the last one ending as `out`), with
+// warp-aggregated atomics whatever the launch's setting (the bits are the
+// same either way).
+template <bool F32>
+__device__ __noinline__ void coop_tally(const SlabDev* pp, mcs::Sink sk, uint32_t rec_off, uint32_t E, int G,
+                                        int hl, int nev, int out) {
+  extern __shared__ unsigned long long s_dyn[];
+  const CoopRec R(s_dyn + rec_off, E);
+  // the lanes of a group tally consecutive events of one history, mostly in
+  // the same bins: their contributions to one slot are summed first
+  sk.agg = true;
+  const SlabDev& p = *pp;
+  for (int e = hl; e < nev; e += G) {
+    const int f = (e == nev - 1 && (out == mcs::kLeakLo || out == mcs::kLeakHi)) ? out : mcs::kCollide;
+    if constexpr (!F32) {
+      const double xe = dval(R.x[e]);
+      const double xn = f == mcs::kCollide ? dval(R.x[e + 1]) : 0.0;
+      mcs::tally64(p, xe, xn, dval(R.m[e]), dval(R.d[e]), dval(R.w[e]), f, sk);
+    } else {
+      const unsigned long long xa = R.x[e];
+      const unsigned long long xb = f == mcs::kCollide ? R.x[e + 1] : 0ull;
+      const unsigned long long dw = R.d[e];
+      mcs::tally32(p, lo_of(xa), hi_of(xa), lo_of(xb), hi_of(xb), hi_of(dw), lo_of(dw), lo_of(R.w[e]), f, sk);
+    }
+  }
+}
+
+// Phase 2: the chain of positions of one history through the round's
+// events, on the history's own lane, until the round ends (kContinue), an
+// event would pass the cap (-1, after `ok` events), or the history leaks or
+// is absorbed; each event's inputs are loaded one event ahead, off the
+// chain.  Out of line, so that the loop's registers are its own.
+struct WalkEnd {
+  double x;
+  float xf, xlo;
+  int nev, out;
+};
+
+template <int M, bool F32>
+__device__ __noinline__ WalkEnd coop_walk(const SlabDev* pp, uint32_t m, uint32_t rec_off, uint32_t E, uint32_t ok,
+                                          double x, float xf, float xlo) {
+  extern __shared__ unsigned long long s_dyn[];
+  const CoopRec R(s_dyn + rec_off, E);
+  const SlabDev p = *pp;
+  int out = mcs::kContinue;
+  uint32_t e = 0;
+  if constexpr (!F32) {
+    R.x[0] = dbits(x);
+    unsigned long long pn = R.p[0], mn = R.m[0], fn = R.f[0];
+    for (; e < E; ++e) {
+      const unsigned long long pc = pn, mc = mn, fc = fn;
+      if (e + 1u < E) { pn = R.p[e + 1u]; mn = R.m[e + 1u]; fn = R.f[e + 1u]; }
+      if (e == ok) { out = -1; break; }
+      double xn;
+      const int f = mcs::advance64(p, x, dval(mc), dval(pc), xn);
+      if (f != mcs::kCollide) { out = f; ++e; break; }
+      x = xn;
+      R.x[e + 1u] = dbits(x);
+      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+    }
+  } else {
+    R.x[0] = pack2(xf, xlo);
+    unsigned long long pn = R.p[0], dn = R.d[0], fn = R.f[0];
+    for (; e < E; ++e) {
+      const unsigned long long pc = pn, dc = dn, fc = fn;
+      if (e + 1u < E) { pn = R.p[e + 1u]; dn = R.d[e + 1u]; fn = R.f[e + 1u]; }
+      if (e == ok) { out = -1; break; }
+      float xn, xnlo;
+      const int f = mcs::advance32(p, xf, xlo, hi_of(dc), lo_of(pc), hi_of(pc),
+                                   [&] { return mcd::u01<M>(R.m[e], m); }, xn, xnlo);
+      if (f != mcs::kCollide) { out = f; ++e; break; }
+      xf = xn;
+      xlo = xnlo;
+      R.x[e + 1u] = pack2(xf, xlo);
+      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+    }
+  }
+  return WalkEnd{x, xf, xlo, (int)e, out};
+}
+
+template <int M, bool F32>
+__device__ __noinline__ void coop_tail(const CoopArgs* cp, const mcd::Affine* tab, uint32_t area_off,
+                                       uint32_t slots, int n_in) {
+  // the kernel's dynamic shared memory, declared again so that the records
+  // are addressed as shared memory
+  extern __shared__ unsigned long long s_dyn[];
+  unsigned long long* const area = s_dyn + area_off;
+  const unsigned kFull = 0xffffffffu;
+  const unsigned lane = threadIdx.x & 31u;
+  const CoopArgs c = *cp;
+  const TailArgs& a = c.t;
+  const mcd::Lcg l = a.lcg;
+  // the warp's histories, handed over through the pool's memory
+  bool alive = (int)lane < n_in;
+  mcs::Rng<M> r{0ull, 0ull};
+  mcs::SlabParticle q{};
+  uint64_t gi = 0, events = 0;
+  const SlabDev* P = c.probs;
+  mcs::Sink sink{nullptr, c.edges, c.widths, c.agg};
+  mcs::LaneCounts lc;
+  lc.prob = -1;
+  lc.clear();
+  if (alive) {
+    const uint32_t pi = pool_get<M>(area + (size_t)lane * kPoolWords, r, q, gi, events);
+    P = c.probs + pi;
+    lc.prob = (int)pi;
+    const uint64_t id = gi - P->hist_begin;
+    sink.base = c.tally + P->tally_offset + mcs::batch_of(id, P->n_hist, P->n_batches) * P->n_bins;
+    if (c.tables) {
+      sink.edges = c.tables + P->tab_off;
+      sink.widths = sink.edges + P->n_bins + 1;
+    }
+  }
+  __syncwarp();
+  for (;;) {
+    const unsigned live = __ballot_sync(kFull, alive);
+    if (live == 0u) break;
+    const int nl = __popc(live);
+    const int kp = coop_groups(nl);
+    const int G = 32 / kp;
+    const int grp = (int)lane / G, hl = (int)lane % G;
+    unsigned m = live;
+    for (int i = 0; i < grp && m != 0u; ++i) m &= m - 1u;
+    const int owner = (grp < nl && m != 0u) ? __ffs(m) - 1 : -1;
+    const int src = owner >= 0 ? owner : (int)lane;
+    const uint32_t E = coop_events(slots, kp);
+    // the owner's history, as every lane of its group sees it
+    const uint64_t x0 = __shfl_sync(kFull, r.x, src);
+    const SlabDev* pp = reinterpret_cast<const SlabDev*>(__shfl_sync(kFull, (unsigned long long)P, src));
+    mcs::Sink sk = sink;
+    sk.base = reinterpret_cast<unsigned long long*>(__shfl_sync(kFull, (unsigned long long)sink.base, src));
+    sk.edges = reinterpret_cast<const double*>(__shfl_sync(kFull, (unsigned long long)sink.edges, src));
+    sk.widths = reinterpret_cast<const double*>(__shfl_sync(kFull, (unsigned long long)sink.widths, src));
+    const double mu0 = __shfl_sync(kFull, q.mu, src), w0 = __shfl_sync(kFull, q.w_mu, src);
+    const float muf0 = __shfl_sync(kFull, q.muf, src), wf0 = __shfl_sync(kFull, q.wf, src);
+    // 1. draw-only values of events 0..E-1 and the direction after event E-1
+    const uint32_t rec_off = area_off + (uint32_t)grp * (E + 1u) * kCoopWords;
+    const CoopRec R(s_dyn + rec_off, E);
+    if (owner >= 0) coop_draws<M, F32>(tab, pp, l, x0, rec_off, E, G, hl, mu0, w0, muf0, wf0);
+    __syncwarp();
+    // 2. the chain of positions, on the history's own lane
+    int nev = 0, out = mcs::kContinue;
+    if ((int)lane == owner) {
+      // events left before the cap (events never passes it)
+      const uint64_t left = a.event_cap - events;
+      const WalkEnd w = coop_walk<M, F32>(P, l.m, rec_off, E, left < E ? (uint32_t)left : E, q.x, q.xf, q.xlo);
+      nev = w.nev;
+      out = w.out;
+      // the counters of the events run: every one a flight; a collision
+      // unless it leaked; then an absorption or a scattering
+      const bool leaked = out == mcs::kLeakLo || out == mcs::kLeakHi;
+      events += (uint64_t)nev;
+      lc.flights += (uint32_t)nev;
+      lc.coll += (uint32_t)nev - (leaked ? 1u : 0u);
+      lc.absn += out == mcs::kAbsorbed ? 1u : 0u;
+      lc.scat += (uint32_t)nev - (leaked || out == mcs::kAbsorbed ? 1u : 0u);
+      lc.llo += out == mcs::kLeakLo ? 1u : 0u;
+      lc.lhi += out == mcs::kLeakHi ? 1u : 0u;
+      lc.capped += out == -1 ? 1u : 0u;
+      if constexpr (!F32) {
+        q.x = w.x;
+        if (out == mcs::kContinue) { q.mu = dval(R.m[E]); q.w_mu = dval(R.w[E]); }
+      } else {
+        q.xf = w.xf;
+        q.xlo = w.xlo;
+        if (out == mcs::kContinue) { q.muf = hi_of(R.d[E]); q.wf = lo_of(R.w[E]); }
+      }
+      const uint32_t e = (uint32_t)nev;
+      // draws taken: three per completed event, one for a leaking flight,
+      // two for an absorbed one, none for a capped event
+      const uint64_t used = out == mcs::kContinue ? 3ull * E
+                          : out == -1 ? 3ull * e
+                          : out == mcs::kAbsorbed ? 3ull * e - 1ull : 3ull * e - 2ull;
+      r.x = mcs::skip_tab(tab, x0, used);
+      r.draws += used;
+    }
+    __syncwarp();
+    nev = __shfl_sync(kFull, nev, src);
+    out = __shfl_sync(kFull, out, src);
+    // 3. the tally contributions of the round's events
+    if (owner >= 0) coop_tally<F32>(pp, sk, rec_off, E, G, hl, nev, out);
+    __syncwarp();
+    if ((int)lane == owner && out != mcs::kContinue) {
+      end_history<M>(a, r, P, gi, lc);
+      alive = false;
+    }
+  }
+  lc.flush_warp(a.counts);
+}
+
 template <int M, bool F32, bool SMEM, bool AGG>
 __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   extern __shared__ unsigned long long s_tally[];
@@ -233,6 +580,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   mcs::SlabParticle q{};
   mcs::Sink sink{nullptr, s_edges, s_widths, AGG};
   uint64_t gi = 0, events = 0;
+  int coop_n = 0;  // histories handed to the cooperative tail (warp-uniform)
 
   for (;;) {
     unsigned dead = __ballot_sync(kFull, !alive);
@@ -310,6 +658,27 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
       }
       const unsigned live = ~dead;
       const int nlive = __popc(live);
+      if (nlive != 0 && nlive <= kCoopMax && hint_active == 1 && hint_n == 0 &&
+          coop_events(a.coop_slots, coop_groups(nlive)) >= kCoopMinEvents) {
+        // the block's last warp with a few long histories: confirm under the
+        // lock that no warp is left to fill the pool, then finish them
+        // together
+        int ok = 0;
+        if (lane == 0 && pool_lock(&ctl.lock, a.lock_attempts)) {
+          ok = (vc.n == 0 && vc.active == 1) ? 1 : 0;
+          pool_unlock(&ctl.lock);
+        }
+        if (__shfl_sync(kFull, ok, 0)) {
+          lc.flush_warp(a.counts);
+          if (alive)
+            pool_put<M>(s_pool + (size_t)__popc(live & lt_mask) * kPoolWords, r, q, gi, events,
+                        (uint32_t)(P - a.probs));
+          __syncwarp();
+          coop_n = nlive;
+          alive = false;
+          break;
+        }
+      }
       if (nlive == 0 || (nlive <= (int)a.donate_max && hint_active > 1 && hint_n + nlive <= (int)a.pool_cap)) {
         int go = 0, n = 0;
         if (lane == 0) {
@@ -361,15 +730,20 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
         else if (outcome == mcs::kLeakHi) ++lc.lhi;
       }
       if (outcome != mcs::kContinue) {
-        lc.draws += r.draws;
-        if (r.draws > lc.maxd) lc.maxd = r.draws;
-        if (P->stride_q != 0 && r.draws > P->stride_q) { ++lc.exh; lc.exd += r.draws - P->stride_q; }
-        if (a.hist_state) a.hist_state[gi] = r.x & l.mask;
-        if (a.hist_draws) a.hist_draws[gi] = r.draws;
+        end_history<M>(TailArgs{a.hist_state, a.hist_draws, a.counts, a.lcg, a.event_cap}, r, P, gi, lc);
         alive = false;
-        if (lc.draws > (1ull << 31)) lc.flush(a.counts);
       }
     }
+  }
+  if (coop_n != 0) {
+    // the arguments through shared memory too: a call with them by value
+    // would put them on the stack of the whole kernel
+    __shared__ CoopArgs s_coop;
+    if (lane == 0)
+      s_coop = CoopArgs{TailArgs{a.hist_state, a.hist_draws, a.counts, a.lcg, a.event_cap}, a.probs,
+                        SMEM ? s_tally : a.tally, a.tables, s_edges, s_widths, AGG};
+    __syncwarp();
+    coop_tail<M, F32>(&s_coop, tab, (uint32_t)(s_pool - s_tally), a.coop_slots, coop_n);
   }
   lc.flush_warp(a.counts);
 
@@ -405,6 +779,7 @@ int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms,
   };
   if (static_smem + dynamic_smem() > (size_t)optin) a.pool_cap = 0;
   if (static_smem + dynamic_smem() > (size_t)optin) a.smem_edges = 0;
+  a.coop_slots = a.pool_cap * (uint32_t)kPoolWords / (uint32_t)kCoopWords;
   const size_t smem = dynamic_smem();
   if (static_smem + smem > (size_t)optin) {
     mci::set_error("slab_history_kernel: %u tally slots do not fit in shared memory", a.smem_slots);

@@ -396,6 +396,78 @@ __device__ __forceinline__ void slab_source(const SlabDev& p, Rng<M>& r, const m
   }
 }
 
+// The end of a flight of the fp64 path: xn = x + pm (pm = d mu, rounded
+// once), and whether it leaves the slab.  mu is never -0 (2u - 1 rounds an
+// exact zero to +0), so its sign is the sign of its bit pattern; x, L and
+// the positions of a forward flight are non-negative.
+__device__ __forceinline__ int advance64(const SlabDev& p, double x, double mu, double pm, double& xn) {
+  xn = __dadd_rn(x, pm);
+  const long long mb = __double_as_longlong(mu);
+  if (mb > 0 && !nn_lt(xn, p.L)) return kLeakHi;
+  if (mb < 0 && __double_as_longlong(xn) <= 0) return kLeakLo;
+  return kCollide;
+}
+
+// The tally of that flight: the track from x to xn, to the face it leaves
+// through, or (mu = 0) the whole distance d in the bin holding x.  Every
+// kind of flight ends in the one call of the bin walk, with its ends chosen
+// first, so that the lanes of a warp whose flights differ in kind still walk
+// the bins together.
+__device__ __forceinline__ void tally64(const SlabDev& p, double x, double xn, double mu, double d, double w_mu,
+                                        int outcome, const Sink& s) {
+  const long long mb = __double_as_longlong(mu);
+  if (outcome == kCollide && mb == 0) { point64(p, x, d, s); return; }
+  double a = x, b = xn;                          // forward flight
+  if (outcome == kLeakHi) b = p.L;
+  else if (outcome == kLeakLo) { a = 0.0; b = x; }
+  else if (mb < 0) { a = xn; b = x; }            // backward flight
+  seg64(p, a, b, w_mu, s);
+}
+
+// The end of a flight of the fp32 path: xn + xnlo = (xf + xlo) + d muf, with
+// pr = d muf rounded and pe its exact error (a fused multiply-add); the sum
+// by TwoSum, the low parts' sum rounded once more (a second-order error).
+// Near a face the leak-or-collide decision is made again in fp64 from the
+// flight's uniform, uf() (called only there).
+template <class UF>
+__device__ __forceinline__ int advance32(const SlabDev& p, float xf, float xlo, float muf, float pr, float pe,
+                                         UF uf, float& xn, float& xnlo) {
+  float s0, t0;
+  two_sum_f(xf, pr, s0, t0);
+  two_sum_f(s0, __fadd_rn(t0, __fadd_rn(xlo, pe)), xn, xnlo);
+  // Guard band: re-decide leak vs collide in fp64 near a face.
+  const bool near_hi = muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
+  const bool near_lo = muf < 0.0f && fabsf(xn) <= p.guard_f;
+  // xn + xnlo >= L (or <= 0) from the pair: the low part decides a tie of the high part
+  bool leak_hi = muf > 0.0f && (xn > p.L_f || (xn == p.L_f && xnlo >= 0.0f));
+  bool leak_lo = muf < 0.0f && (xn < 0.0f || (xn == 0.0f && xnlo <= 0.0f));
+  if (near_hi || near_lo) {
+    const double d64 = __dmul_rn(-mclog::log1m(uf()), p.inv_st);
+    const double x64 = __dadd_rn((double)xf, (double)xlo);
+    const double xn64 = __dadd_rn(x64, __dmul_rn(d64, (double)muf));
+    leak_hi = muf > 0.0f && xn64 >= p.L;
+    leak_lo = muf < 0.0f && xn64 <= 0.0;
+    xn = __double2float_rn(xn64);
+    if (!leak_hi && !leak_lo) {
+      // keep the collision site's high part strictly inside
+      if (xn >= p.L_f) xn = __int_as_float(__float_as_int(p.L_f) - 1);
+      if (xn <= 0.0f) xn = 1.0e-30f;
+    }
+    xnlo = __double2float_rn(__dsub_rn(xn64, (double)xn));
+  }
+  return leak_hi ? kLeakHi : (leak_lo ? kLeakLo : kCollide);
+}
+
+__device__ __forceinline__ void tally32(const SlabDev& p, float xf, float xlo, float xn, float xnlo, float muf,
+                                        float d, float wf, int outcome, const Sink& s) {
+  if (outcome == kCollide && muf == 0.0f) { point32(p, xf, d, s); return; }
+  float ah = xf, al = xlo, bh = xn, bl = xnlo;   // forward flight
+  if (outcome == kLeakHi) { bh = p.L_f; bl = 0.0f; }
+  else if (outcome == kLeakLo) { ah = 0.0f; al = 0.0f; bh = xf; bl = xlo; }
+  else if (muf < 0.0f) { ah = xn; al = xnlo; bh = xf; bl = xlo; }  // backward flight
+  seg32(p, ah, al, bh, bl, wf, s);
+}
+
 // One flight: sample the distance, tally the track, and either leak
 // (kLeakLo / kLeakHi) or stop at the collision site (kCollide).
 template <int M, bool F32>
@@ -403,58 +475,25 @@ __device__ __forceinline__ int slab_flight(const SlabDev& p, Rng<M>& r, const mc
                                            const Sink& s) {
   if constexpr (!F32) {
     const double d = __dmul_rn(-mclog::log1m_n(r.next_n(l)), p.inv_st);
-    const double xn = __dadd_rn(q.x, __dmul_rn(d, q.mu));
-    // mu is never -0 (2u - 1 rounds an exact zero to +0), so its sign is the
-    // sign of its bit pattern; x, L and the positions of a forward flight are
-    // non-negative.
-    const long long mb = __double_as_longlong(q.mu);
-    if (mb > 0 && !nn_lt(xn, p.L)) { seg64(p, q.x, p.L, q.w_mu, s); return kLeakHi; }
-    if (mb < 0 && __double_as_longlong(xn) <= 0) { seg64(p, 0.0, q.x, q.w_mu, s); return kLeakLo; }
-    if (mb == 0) point64(p, q.x, d, s);
-    else if (mb > 0) seg64(p, q.x, xn, q.w_mu, s);
-    else seg64(p, xn, q.x, q.w_mu, s);
-    q.x = xn;
+    double xn;
+    const int f = advance64(p, q.x, q.mu, __dmul_rn(d, q.mu), xn);
+    tally64(p, q.x, xn, q.mu, d, q.w_mu, f, s);
+    if (f == kCollide) q.x = xn;
+    return f;
   } else {
     const double u = r.next(l);
     const float d = flight_f32(u) * p.inv_st_f;
-    // xn + xnlo = (xf + xlo) + d muf: the product's exact error from a fused
-    // multiply-add, the sum by TwoSum; the low parts' sum rounds once more,
-    // a second-order error.
     const float pr = __fmul_rn(d, q.muf);
     const float pe = __fmaf_rn(d, q.muf, -pr);
-    float s0, t0;
-    two_sum_f(q.xf, pr, s0, t0);
     float xn, xnlo;
-    two_sum_f(s0, __fadd_rn(t0, __fadd_rn(q.xlo, pe)), xn, xnlo);
-    // Guard band: re-decide leak vs collide in fp64 near a face.
-    const bool near_hi = q.muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
-    const bool near_lo = q.muf < 0.0f && fabsf(xn) <= p.guard_f;
-    // xn + xnlo >= L (or <= 0) from the pair: the low part decides a tie of the high part
-    bool leak_hi = q.muf > 0.0f && (xn > p.L_f || (xn == p.L_f && xnlo >= 0.0f));
-    bool leak_lo = q.muf < 0.0f && (xn < 0.0f || (xn == 0.0f && xnlo <= 0.0f));
-    if (near_hi || near_lo) {
-      const double d64 = __dmul_rn(-mclog::log1m(u), p.inv_st);
-      const double x64 = __dadd_rn((double)q.xf, (double)q.xlo);
-      const double xn64 = __dadd_rn(x64, __dmul_rn(d64, (double)q.muf));
-      leak_hi = q.muf > 0.0f && xn64 >= p.L;
-      leak_lo = q.muf < 0.0f && xn64 <= 0.0;
-      xn = __double2float_rn(xn64);
-      if (!leak_hi && !leak_lo) {
-        // keep the collision site's high part strictly inside
-        if (xn >= p.L_f) xn = __int_as_float(__float_as_int(p.L_f) - 1);
-        if (xn <= 0.0f) xn = 1.0e-30f;
-      }
-      xnlo = __double2float_rn(__dsub_rn(xn64, (double)xn));
+    const int f = advance32(p, q.xf, q.xlo, q.muf, pr, pe, [u] { return u; }, xn, xnlo);
+    tally32(p, q.xf, q.xlo, xn, xnlo, q.muf, d, q.wf, f, s);
+    if (f == kCollide) {
+      q.xf = xn;
+      q.xlo = xnlo;
     }
-    if (leak_hi) { seg32(p, q.xf, q.xlo, p.L_f, 0.0f, q.wf, s); return kLeakHi; }
-    if (leak_lo) { seg32(p, 0.0f, 0.0f, q.xf, q.xlo, q.wf, s); return kLeakLo; }
-    if (q.muf == 0.0f) point32(p, q.xf, d, s);
-    else if (q.muf > 0.0f) seg32(p, q.xf, q.xlo, xn, xnlo, q.wf, s);
-    else seg32(p, xn, xnlo, q.xf, q.xlo, q.wf, s);
-    q.xf = xn;
-    q.xlo = xnlo;
+    return f;
   }
-  return kCollide;
 }
 
 // One collision at the current site: absorption (kAbsorbed) or isotropic

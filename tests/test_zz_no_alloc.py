@@ -52,6 +52,40 @@ def test_static_entry_matches_context_entry_on_consecutive_calls():
     ctx.close()
 
 
+def test_static_entry_matches_the_oracle(oracle):
+    """The static entry against the oracle directly: final state and draw
+    count of every history bit-exact, counters exact, int64 bins within the
+    1e-6 relative bar, for several problems in one call."""
+    import torch
+    import paper_2403_06362_gb300 as mc
+    from paper_2403_06362_gb300 import _build
+    _build.build()
+    probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=12, max_histories=3000)
+    total = sum(p["n_histories"] for p in probs)
+    arr = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    got = mc.Tally(W.tally_slots(probs), len(probs), n_histories=total)
+    mc.mc_transport_run_static(mc.make_lcg(), arr, mc.mc_run_config(), got.c)
+    torch.cuda.synchronize()
+    tally = np.zeros(W.tally_slots(probs), dtype=np.int64)
+    hs, hd, counts = [], [], []
+    for p in probs:
+        c = np.zeros(oracle.NCOUNT, dtype=np.uint64)
+        r = oracle.slab_run(oracle.Lcg(m=W.LCG_M, pad=0, g=W.LCG_G, c=W.LCG_C),
+                            W.to_oracle_problem(p, oracle), tally=tally, counts=c, per_history=True)
+        hs.append(r["hist_state"])
+        hd.append(r["hist_draws"])
+        counts.append(c)
+    assert np.array_equal(got.hist_state.cpu().numpy().view(np.uint64),
+                          np.concatenate(hs).astype(np.uint64))
+    assert np.array_equal(got.hist_draws.cpu().numpy().view(np.uint64),
+                          np.concatenate(hd).astype(np.uint64))
+    gc = got.counts.cpu().numpy().view(np.uint64).reshape(len(probs), -1)
+    assert np.array_equal(gc[:, :14], np.array(counts)[:, :14])
+    gb = got.bins.cpu().numpy().astype(np.float64)
+    ob = tally.astype(np.float64)
+    assert np.all(np.abs(gb - ob) <= TOL * np.abs(ob))
+
+
 def test_static_entry_rejects_too_many_problems():
     import paper_2403_06362_gb300 as mc
     from paper_2403_06362_gb300 import _build
