@@ -193,16 +193,10 @@ struct TailArgs {
   uint64_t event_cap;
 };
 
-// The cooperative tail's view of the launch: the tail's own fields and what
-// it needs to rebuild a history's tally sink.
+// The cooperative tail's view of the launch.
 struct CoopArgs {
   TailArgs t;
   const SlabDev* probs;
-  unsigned long long* tally;  // the block's staged tally or the global one
-  const double* tables;       // per-problem edge and width tables (nullable)
-  const double* edges;        // single problem: edges and widths in shared memory (nullable)
-  const double* widths;
-  bool agg;
 };
 
 // End of a history: its draws into the lane's counters, its final state and
@@ -234,19 +228,19 @@ __device__ __forceinline__ void end_history(const TailArgs& t, const mcs::Rng<M>
 //      distance d_e, the product p_e = d_e mu_e, the absorption test and the
 //      direction mu_{e+1} with its tally weight, jumping the stream to draw
 //      3e with the maps of 2^j steps;
-//   2. the history's own lane runs the chain of positions alone, x_{e+1} =
-//      x_e + p_e and the face tests, until the round ends or the history
-//      does (an event cap, a leak, an absorption);
+//   2. one lane runs the chain of positions alone, x_{e+1} = x_e + p_e and
+//      the face tests, until the round ends or the history does (an event
+//      cap, a leak, an absorption);
 //   3. the group's lanes make the tally contributions of the round's events.
 // Every value comes from the same function, with the same operands, as in
 // the one-lane path, so the draws, tallies and counters are the same bits.
-// The round's event records sit in the (then empty) pool's shared memory.
-// The warp's histories and the launch's arguments come in through shared
-// memory, and the function, kept out of line, runs the histories to their
-// ends and flushes the lanes' counters: the main loop ends first, and no
-// register of it stays live across the call.
-constexpr int kCoopMax = 4;        // live histories at most
-constexpr int kCoopWords = 6;      // 8-byte words per event record
+// The histories' state, the launch's arguments and the rounds' event
+// records sit in the (then empty) pool's shared memory, and each phase is a
+// function of its own that takes them from there: the main loop has ended,
+// and almost nothing stays in registers across the calls.
+constexpr int kCoopMax = 4;            // live histories at most
+constexpr int kCoopHistWords = 16;     // 8-byte words per history record
+constexpr int kCoopWords = 6;          // 8-byte words per event record
 constexpr uint32_t kCoopEvents = 128;  // events per history and round at most
 constexpr uint32_t kCoopMinEvents = 8;
 
@@ -255,6 +249,12 @@ __device__ __forceinline__ int coop_groups(int nlive) { return nlive <= 1 ? 1 : 
 __device__ __forceinline__ uint32_t coop_events(uint32_t slots, int kp) {
   const uint32_t per = slots / (uint32_t)kp;  // records per history: E events and the direction after them
   return per > 1u ? min(kCoopEvents, per - 1u) : 0u;
+}
+
+// Event records the pool's memory holds beside the history records.
+__host__ __device__ __forceinline__ uint32_t coop_slots_of(uint32_t pool_words) {
+  const uint32_t h = (uint32_t)(kCoopMax * kCoopHistWords);
+  return pool_words > h ? (pool_words - h) / (uint32_t)kCoopWords : 0u;
 }
 
 __device__ __forceinline__ mcd::Affine affine_steps(const mcd::Affine* tab, uint64_t k) {
@@ -275,6 +275,37 @@ __device__ __forceinline__ float hi_of(unsigned long long w) { return __uint_as_
 __device__ __forceinline__ unsigned long long dbits(double v) { return (unsigned long long)__double_as_longlong(v); }
 __device__ __forceinline__ double dval(unsigned long long w) { return __longlong_as_double((long long)w); }
 
+// A history's record: its stream, particle, ids, tally sink and the counts
+// of its events in the tail.
+struct CoopHist {
+  unsigned long long* w;
+  enum {
+    kX = 0,      // stream state
+    kDraws,      // draws taken
+    kPos,        // fp64 x (fp32: xf, xlo)
+    kDir,        // fp64 mu (fp32: muf, wf)
+    kW,          // fp64 2^32 / |mu|
+    kGi,         // global history index
+    kEvents,     // flights flown
+    kProb,       // problem index; bit 32: live
+    kBase,       // tally row
+    kEdges,      // edge and width tables (null: computed)
+    kWidths,
+    kFlights,    // counts of the tail's events
+    kColl,
+    kScat,
+    kEnd,        // last round: events run (low half) and how the last one ended (high half)
+    kSpare
+  };
+  __device__ __forceinline__ explicit CoopHist(unsigned long long* p) : w(p) {}
+  __device__ __forceinline__ bool live() const { return (w[kProb] >> 32) != 0ull; }
+  __device__ __forceinline__ const SlabDev* prob(const SlabDev* probs) const { return probs + (uint32_t)w[kProb]; }
+  __device__ __forceinline__ mcs::Sink sink(bool agg) const {
+    return mcs::Sink{reinterpret_cast<unsigned long long*>(w[kBase]), reinterpret_cast<const double*>(w[kEdges]),
+                     reinterpret_cast<const double*>(w[kWidths]), agg};
+  }
+};
+
 // The records of one history's round, six arrays of E + 1 words.
 struct CoopRec {
   unsigned long long* p;  // p_e = d_e mu_e (fp32: pr and pe, the product and its error)
@@ -288,22 +319,23 @@ struct CoopRec {
         f(r + 5u * (E + 1u)) {}
 };
 
-// Phase 1 of a round of the cooperative tail, on lane hl of the G lanes of
-// a history's group: the draw-only values of the events e = hl, hl + G, ...
-// (out of line: the logarithm and the reciprocal keep their registers to
-// themselves).
+// Phase 1, on lane hl of the G lanes of a history's group: the draw-only
+// values of the events e = hl, hl + G, ... <= E.
 template <int M, bool F32>
-__device__ __noinline__ void coop_draws(const mcd::Affine* tab, const SlabDev* pp, mcd::Lcg l, uint64_t x0,
-                                        uint32_t rec_off, uint32_t E, int G, int hl, double mu0, double w0,
-                                        float muf0, float wf0) {
+__device__ __noinline__ void coop_draws(const CoopArgs* c, const mcd::Affine* tab, uint32_t hist_off,
+                                        uint32_t rec_off, uint32_t E, int G, int hl) {
   extern __shared__ unsigned long long s_dyn[];
+  const CoopHist H(s_dyn + hist_off);
   const CoopRec R(s_dyn + rec_off, E);
-  const SlabDev& p = *pp;
+  const mcd::Lcg l = c->t.lcg;
+  const SlabDev& p = *H.prob(c->probs);
+  const uint64_t x0 = H.w[CoopHist::kX];
+  const unsigned long long dir0 = H.w[CoopHist::kDir], w0 = H.w[CoopHist::kW];
   const mcd::Affine step3g = affine_steps(tab, 3ull * (uint64_t)G);
   uint64_t xs = mcs::skip_tab(tab, x0, 3ull * (uint64_t)hl);  // the state after 3e draws
   for (uint32_t e = (uint32_t)hl; e <= E; e += (uint32_t)G) {
     if constexpr (!F32) {
-      double mu = mu0, w = w0;
+      double mu = dval(dir0), w = dval(w0);
       if (e != 0u) {
         mu = mcx::two_u_minus_1(mcd::u53<M>(xs, l.m));
         w = mcs::fix_per_mu(mu);
@@ -318,7 +350,7 @@ __device__ __noinline__ void coop_draws(const mcd::Affine* tab, const SlabDev* p
         R.f[e] = mcd::u53<M>(mcd::lcg_step(sd, l.g, l.c), l.m) < p.p_abs_n ? 1ull : 0ull;
       }
     } else {
-      float muf = muf0, wf = wf0;
+      float muf = lo_of(dir0), wf = hi_of(dir0);
       if (e != 0u) {
         muf = mcs::mu_f32(mcd::u53<M>(xs, l.m));
         wf = muf != 0.0f ? __frcp_rn(fabsf(muf)) : 0.0f;
@@ -339,19 +371,118 @@ __device__ __noinline__ void coop_draws(const mcd::Affine* tab, const SlabDev* p
   }
 }
 
-// Phase 3: the tally contributions of the round's events e = hl, hl + G, ...
-// of the nev events the history ran (the last one ending as `out`), with
-// warp-aggregated atomics whatever the launch's setting (the bits are the
-// same either way).
-template <bool F32>
-__device__ __noinline__ void coop_tally(const SlabDev* pp, mcs::Sink sk, uint32_t rec_off, uint32_t E, int G,
-                                        int hl, int nev, int out) {
+// Phase 2, on one lane: the chain of positions through the round's events,
+// until the round ends (kContinue), an event would pass the cap (-1), or the
+// history leaks or is absorbed; each event's inputs are loaded one event
+// ahead, off the chain.  Then the history's record moves on by the events
+// run, and a history that ended is counted and written out.
+template <int M, bool F32>
+__device__ __noinline__ void coop_walk(const CoopArgs* c, const mcd::Affine* tab, uint32_t hist_off,
+                                       uint32_t rec_off, uint32_t E) {
   extern __shared__ unsigned long long s_dyn[];
+  const CoopHist H(s_dyn + hist_off);
   const CoopRec R(s_dyn + rec_off, E);
-  // the lanes of a group tally consecutive events of one history, mostly in
-  // the same bins: their contributions to one slot are summed first
-  sk.agg = true;
-  const SlabDev& p = *pp;
+  const SlabDev* P = H.prob(c->probs);
+  const SlabDev p = *P;
+  const uint64_t events = H.w[CoopHist::kEvents];
+  const uint64_t left = c->t.event_cap - events;  // events never pass the cap
+  const uint32_t ok = left < E ? (uint32_t)left : E;
+  int out = mcs::kContinue;
+  uint32_t e = 0;
+  if constexpr (!F32) {
+    double x = dval(H.w[CoopHist::kPos]);
+    R.x[0] = dbits(x);
+    unsigned long long pn = R.p[0], mn = R.m[0], fn = R.f[0];
+    for (; e < E; ++e) {
+      const unsigned long long pc = pn, mc = mn, fc = fn;
+      if (e + 1u < E) { pn = R.p[e + 1u]; mn = R.m[e + 1u]; fn = R.f[e + 1u]; }
+      if (e == ok) { out = -1; break; }
+      double xn;
+      const int f = mcs::advance64(p, x, dval(mc), dval(pc), xn);
+      if (f != mcs::kCollide) { out = f; ++e; break; }
+      x = xn;
+      R.x[e + 1u] = dbits(x);
+      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+    }
+    H.w[CoopHist::kPos] = dbits(x);
+    if (out == mcs::kContinue) { H.w[CoopHist::kDir] = R.m[E]; H.w[CoopHist::kW] = R.w[E]; }
+  } else {
+    const unsigned long long pos = H.w[CoopHist::kPos];
+    float xf = lo_of(pos), xlo = hi_of(pos);
+    R.x[0] = pos;
+    const uint32_t m = c->t.lcg.m;
+    unsigned long long pn = R.p[0], dn = R.d[0], fn = R.f[0];
+    for (; e < E; ++e) {
+      const unsigned long long pc = pn, dc = dn, fc = fn;
+      if (e + 1u < E) { pn = R.p[e + 1u]; dn = R.d[e + 1u]; fn = R.f[e + 1u]; }
+      if (e == ok) { out = -1; break; }
+      float xn, xnlo;
+      const int f = mcs::advance32(p, xf, xlo, hi_of(dc), lo_of(pc), hi_of(pc),
+                                   [&] { return mcd::u01<M>(R.m[e], m); }, xn, xnlo);
+      if (f != mcs::kCollide) { out = f; ++e; break; }
+      xf = xn;
+      xlo = xnlo;
+      R.x[e + 1u] = pack2(xf, xlo);
+      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+    }
+    H.w[CoopHist::kPos] = pack2(xf, xlo);
+    if (out == mcs::kContinue) H.w[CoopHist::kDir] = pack2(hi_of(R.d[E]), lo_of(R.w[E]));
+  }
+  // every event run is a flight; a collision unless it leaked; then an
+  // absorption or a scattering
+  const bool leaked = out == mcs::kLeakLo || out == mcs::kLeakHi;
+  H.w[CoopHist::kEvents] = events + e;
+  H.w[CoopHist::kFlights] += e;
+  H.w[CoopHist::kColl] += e - (leaked ? 1u : 0u);
+  H.w[CoopHist::kScat] += e - (leaked || out == mcs::kAbsorbed ? 1u : 0u);
+  H.w[CoopHist::kEnd] = (unsigned long long)e | ((unsigned long long)(uint32_t)out << 32);
+  // draws taken: three per completed event, one for a leaking flight, two
+  // for an absorbed one, none for a capped event
+  const uint64_t used = out == mcs::kContinue ? 3ull * E
+                      : out == -1 ? 3ull * e
+                      : out == mcs::kAbsorbed ? 3ull * e - 1ull : 3ull * e - 2ull;
+  const uint64_t x = mcs::skip_tab(tab, H.w[CoopHist::kX], used);
+  const uint64_t draws = H.w[CoopHist::kDraws] + used;
+  H.w[CoopHist::kX] = x;
+  H.w[CoopHist::kDraws] = draws;
+  if (out == mcs::kContinue) return;
+  // the history's end: its counts as the one-lane path would flush them
+  const uint32_t pi = (uint32_t)H.w[CoopHist::kProb];
+  unsigned long long* cnt = c->t.counts + (size_t)pi * MC_NCOUNT;
+  atomicAdd(cnt + MC_C_FLIGHTS, H.w[CoopHist::kFlights]);
+  if (H.w[CoopHist::kColl]) atomicAdd(cnt + MC_C_COLLISIONS, H.w[CoopHist::kColl]);
+  if (H.w[CoopHist::kScat]) atomicAdd(cnt + MC_C_SCATTERS, H.w[CoopHist::kScat]);
+  if (out == mcs::kAbsorbed) atomicAdd(cnt + MC_C_ABSORPTIONS, 1ull);
+  else if (out == mcs::kLeakLo) atomicAdd(cnt + MC_C_LEAK_LO, 1ull);
+  else if (out == mcs::kLeakHi) atomicAdd(cnt + MC_C_LEAK_HI, 1ull);
+  else atomicAdd(cnt + MC_C_CAPPED, 1ull);
+  atomicAdd(cnt + MC_C_DRAWS, draws);
+  atomicMax(cnt + MC_C_MAX_DRAWS, draws);
+  if (p.stride_q != 0 && draws > p.stride_q) {
+    atomicAdd(cnt + MC_C_EXCEED_HIST, 1ull);
+    atomicAdd(cnt + MC_C_EXCEED_DRAWS, draws - p.stride_q);
+  }
+  const uint64_t gi = H.w[CoopHist::kGi];
+  if (c->t.hist_state) c->t.hist_state[gi] = x & c->t.lcg.mask;
+  if (c->t.hist_draws) c->t.hist_draws[gi] = draws;
+  H.w[CoopHist::kProb] = pi;  // no longer live
+}
+
+// Phase 3, on lane hl of the group: the tally contributions of the round's
+// events e = hl, hl + G, ... of those the history ran, with warp-aggregated
+// atomics whatever the launch's setting (the bits are the same either way):
+// the lanes of a group tally consecutive events of one history, mostly in
+// the same bins.
+template <bool F32>
+__device__ __noinline__ void coop_tally(const CoopArgs* c, uint32_t hist_off, uint32_t rec_off, uint32_t E, int G,
+                                        int hl) {
+  extern __shared__ unsigned long long s_dyn[];
+  const CoopHist H(s_dyn + hist_off);
+  const CoopRec R(s_dyn + rec_off, E);
+  const SlabDev& p = *H.prob(c->probs);
+  const mcs::Sink sk = H.sink(true);
+  const unsigned long long end = H.w[CoopHist::kEnd];
+  const int nev = (int)(uint32_t)end, out = (int)(uint32_t)(end >> 32);
   for (int e = hl; e < nev; e += G) {
     const int f = (e == nev - 1 && (out == mcs::kLeakLo || out == mcs::kLeakHi)) ? out : mcs::kCollide;
     if constexpr (!F32) {
@@ -367,95 +498,18 @@ __device__ __noinline__ void coop_tally(const SlabDev* pp, mcs::Sink sk, uint32_
   }
 }
 
-// Phase 2: the chain of positions of one history through the round's
-// events, on the history's own lane, until the round ends (kContinue), an
-// event would pass the cap (-1, after `ok` events), or the history leaks or
-// is absorbed; each event's inputs are loaded one event ahead, off the
-// chain.  Out of line, so that the loop's registers are its own.
-struct WalkEnd {
-  double x;
-  float xf, xlo;
-  int nev, out;
-};
-
+// The rounds, warp-uniform, over the n_in history records at area_off.
 template <int M, bool F32>
-__device__ __noinline__ WalkEnd coop_walk(const SlabDev* pp, uint32_t m, uint32_t rec_off, uint32_t E, uint32_t ok,
-                                          double x, float xf, float xlo) {
-  extern __shared__ unsigned long long s_dyn[];
-  const CoopRec R(s_dyn + rec_off, E);
-  const SlabDev p = *pp;
-  int out = mcs::kContinue;
-  uint32_t e = 0;
-  if constexpr (!F32) {
-    R.x[0] = dbits(x);
-    unsigned long long pn = R.p[0], mn = R.m[0], fn = R.f[0];
-    for (; e < E; ++e) {
-      const unsigned long long pc = pn, mc = mn, fc = fn;
-      if (e + 1u < E) { pn = R.p[e + 1u]; mn = R.m[e + 1u]; fn = R.f[e + 1u]; }
-      if (e == ok) { out = -1; break; }
-      double xn;
-      const int f = mcs::advance64(p, x, dval(mc), dval(pc), xn);
-      if (f != mcs::kCollide) { out = f; ++e; break; }
-      x = xn;
-      R.x[e + 1u] = dbits(x);
-      if (fc) { out = mcs::kAbsorbed; ++e; break; }
-    }
-  } else {
-    R.x[0] = pack2(xf, xlo);
-    unsigned long long pn = R.p[0], dn = R.d[0], fn = R.f[0];
-    for (; e < E; ++e) {
-      const unsigned long long pc = pn, dc = dn, fc = fn;
-      if (e + 1u < E) { pn = R.p[e + 1u]; dn = R.d[e + 1u]; fn = R.f[e + 1u]; }
-      if (e == ok) { out = -1; break; }
-      float xn, xnlo;
-      const int f = mcs::advance32(p, xf, xlo, hi_of(dc), lo_of(pc), hi_of(pc),
-                                   [&] { return mcd::u01<M>(R.m[e], m); }, xn, xnlo);
-      if (f != mcs::kCollide) { out = f; ++e; break; }
-      xf = xn;
-      xlo = xnlo;
-      R.x[e + 1u] = pack2(xf, xlo);
-      if (fc) { out = mcs::kAbsorbed; ++e; break; }
-    }
-  }
-  return WalkEnd{x, xf, xlo, (int)e, out};
-}
-
-template <int M, bool F32>
-__device__ __noinline__ void coop_tail(const CoopArgs* cp, const mcd::Affine* tab, uint32_t area_off,
+__device__ __noinline__ void coop_tail(const CoopArgs* c, const mcd::Affine* tab, uint32_t area_off,
                                        uint32_t slots, int n_in) {
-  // the kernel's dynamic shared memory, declared again so that the records
-  // are addressed as shared memory
   extern __shared__ unsigned long long s_dyn[];
-  unsigned long long* const area = s_dyn + area_off;
-  const unsigned kFull = 0xffffffffu;
   const unsigned lane = threadIdx.x & 31u;
-  const CoopArgs c = *cp;
-  const TailArgs& a = c.t;
-  const mcd::Lcg l = a.lcg;
-  // the warp's histories, handed over through the pool's memory
-  bool alive = (int)lane < n_in;
-  mcs::Rng<M> r{0ull, 0ull};
-  mcs::SlabParticle q{};
-  uint64_t gi = 0, events = 0;
-  const SlabDev* P = c.probs;
-  mcs::Sink sink{nullptr, c.edges, c.widths, c.agg};
-  mcs::LaneCounts lc;
-  lc.prob = -1;
-  lc.clear();
-  if (alive) {
-    const uint32_t pi = pool_get<M>(area + (size_t)lane * kPoolWords, r, q, gi, events);
-    P = c.probs + pi;
-    lc.prob = (int)pi;
-    const uint64_t id = gi - P->hist_begin;
-    sink.base = c.tally + P->tally_offset + mcs::batch_of(id, P->n_hist, P->n_batches) * P->n_bins;
-    if (c.tables) {
-      sink.edges = c.tables + P->tab_off;
-      sink.widths = sink.edges + P->n_bins + 1;
-    }
-  }
-  __syncwarp();
+  const uint32_t rec_base = area_off + (uint32_t)(kCoopMax * kCoopHistWords);
   for (;;) {
-    const unsigned live = __ballot_sync(kFull, alive);
+    __syncwarp();
+    unsigned live = 0u;
+    for (int h = 0; h < n_in; ++h)
+      if (CoopHist(s_dyn + area_off + (uint32_t)h * kCoopHistWords).live()) live |= 1u << h;
     if (live == 0u) break;
     const int nl = __popc(live);
     const int kp = coop_groups(nl);
@@ -463,71 +517,17 @@ __device__ __noinline__ void coop_tail(const CoopArgs* cp, const mcd::Affine* ta
     const int grp = (int)lane / G, hl = (int)lane % G;
     unsigned m = live;
     for (int i = 0; i < grp && m != 0u; ++i) m &= m - 1u;
-    const int owner = (grp < nl && m != 0u) ? __ffs(m) - 1 : -1;
-    const int src = owner >= 0 ? owner : (int)lane;
+    const int h = (grp < nl && m != 0u) ? __ffs(m) - 1 : -1;
     const uint32_t E = coop_events(slots, kp);
-    // the owner's history, as every lane of its group sees it
-    const uint64_t x0 = __shfl_sync(kFull, r.x, src);
-    const SlabDev* pp = reinterpret_cast<const SlabDev*>(__shfl_sync(kFull, (unsigned long long)P, src));
-    mcs::Sink sk = sink;
-    sk.base = reinterpret_cast<unsigned long long*>(__shfl_sync(kFull, (unsigned long long)sink.base, src));
-    sk.edges = reinterpret_cast<const double*>(__shfl_sync(kFull, (unsigned long long)sink.edges, src));
-    sk.widths = reinterpret_cast<const double*>(__shfl_sync(kFull, (unsigned long long)sink.widths, src));
-    const double mu0 = __shfl_sync(kFull, q.mu, src), w0 = __shfl_sync(kFull, q.w_mu, src);
-    const float muf0 = __shfl_sync(kFull, q.muf, src), wf0 = __shfl_sync(kFull, q.wf, src);
-    // 1. draw-only values of events 0..E-1 and the direction after event E-1
-    const uint32_t rec_off = area_off + (uint32_t)grp * (E + 1u) * kCoopWords;
-    const CoopRec R(s_dyn + rec_off, E);
-    if (owner >= 0) coop_draws<M, F32>(tab, pp, l, x0, rec_off, E, G, hl, mu0, w0, muf0, wf0);
+    const uint32_t hist_off = area_off + (uint32_t)(h < 0 ? 0 : h) * kCoopHistWords;
+    const uint32_t rec_off = rec_base + (uint32_t)grp * (E + 1u) * kCoopWords;
     __syncwarp();
-    // 2. the chain of positions, on the history's own lane
-    int nev = 0, out = mcs::kContinue;
-    if ((int)lane == owner) {
-      // events left before the cap (events never passes it)
-      const uint64_t left = a.event_cap - events;
-      const WalkEnd w = coop_walk<M, F32>(P, l.m, rec_off, E, left < E ? (uint32_t)left : E, q.x, q.xf, q.xlo);
-      nev = w.nev;
-      out = w.out;
-      // the counters of the events run: every one a flight; a collision
-      // unless it leaked; then an absorption or a scattering
-      const bool leaked = out == mcs::kLeakLo || out == mcs::kLeakHi;
-      events += (uint64_t)nev;
-      lc.flights += (uint32_t)nev;
-      lc.coll += (uint32_t)nev - (leaked ? 1u : 0u);
-      lc.absn += out == mcs::kAbsorbed ? 1u : 0u;
-      lc.scat += (uint32_t)nev - (leaked || out == mcs::kAbsorbed ? 1u : 0u);
-      lc.llo += out == mcs::kLeakLo ? 1u : 0u;
-      lc.lhi += out == mcs::kLeakHi ? 1u : 0u;
-      lc.capped += out == -1 ? 1u : 0u;
-      if constexpr (!F32) {
-        q.x = w.x;
-        if (out == mcs::kContinue) { q.mu = dval(R.m[E]); q.w_mu = dval(R.w[E]); }
-      } else {
-        q.xf = w.xf;
-        q.xlo = w.xlo;
-        if (out == mcs::kContinue) { q.muf = hi_of(R.d[E]); q.wf = lo_of(R.w[E]); }
-      }
-      const uint32_t e = (uint32_t)nev;
-      // draws taken: three per completed event, one for a leaking flight,
-      // two for an absorbed one, none for a capped event
-      const uint64_t used = out == mcs::kContinue ? 3ull * E
-                          : out == -1 ? 3ull * e
-                          : out == mcs::kAbsorbed ? 3ull * e - 1ull : 3ull * e - 2ull;
-      r.x = mcs::skip_tab(tab, x0, used);
-      r.draws += used;
-    }
+    if (h >= 0) coop_draws<M, F32>(c, tab, hist_off, rec_off, E, G, hl);
     __syncwarp();
-    nev = __shfl_sync(kFull, nev, src);
-    out = __shfl_sync(kFull, out, src);
-    // 3. the tally contributions of the round's events
-    if (owner >= 0) coop_tally<F32>(pp, sk, rec_off, E, G, hl, nev, out);
+    if (h >= 0 && hl == 0) coop_walk<M, F32>(c, tab, hist_off, rec_off, E);
     __syncwarp();
-    if ((int)lane == owner && out != mcs::kContinue) {
-      end_history<M>(a, r, P, gi, lc);
-      alive = false;
-    }
+    if (h >= 0) coop_tally<F32>(c, hist_off, rec_off, E, G, hl);
   }
-  lc.flush_warp(a.counts);
 }
 
 template <int M, bool F32, bool SMEM, bool AGG>
@@ -670,10 +670,21 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
         }
         if (__shfl_sync(kFull, ok, 0)) {
           lc.flush_warp(a.counts);
-          if (alive)
-            pool_put<M>(s_pool + (size_t)__popc(live & lt_mask) * kPoolWords, r, q, gi, events,
-                        (uint32_t)(P - a.probs));
-          __syncwarp();
+          if (alive) {
+            CoopHist H(s_pool + (size_t)__popc(live & lt_mask) * kCoopHistWords);
+            H.w[CoopHist::kX] = r.x;
+            H.w[CoopHist::kDraws] = r.draws;
+            H.w[CoopHist::kPos] = F32 ? pack2(q.xf, q.xlo) : dbits(q.x);
+            H.w[CoopHist::kDir] = F32 ? pack2(q.muf, q.wf) : dbits(q.mu);
+            H.w[CoopHist::kW] = dbits(q.w_mu);
+            H.w[CoopHist::kGi] = gi;
+            H.w[CoopHist::kEvents] = events;
+            H.w[CoopHist::kProb] = (uint64_t)(uint32_t)(P - a.probs) | (1ull << 32);
+            H.w[CoopHist::kBase] = reinterpret_cast<unsigned long long>(sink.base);
+            H.w[CoopHist::kEdges] = reinterpret_cast<unsigned long long>(sink.edges);
+            H.w[CoopHist::kWidths] = reinterpret_cast<unsigned long long>(sink.widths);
+            H.w[CoopHist::kFlights] = H.w[CoopHist::kColl] = H.w[CoopHist::kScat] = 0ull;
+          }
           coop_n = nlive;
           alive = false;
           break;
@@ -739,9 +750,7 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
     // the arguments through shared memory too: a call with them by value
     // would put them on the stack of the whole kernel
     __shared__ CoopArgs s_coop;
-    if (lane == 0)
-      s_coop = CoopArgs{TailArgs{a.hist_state, a.hist_draws, a.counts, a.lcg, a.event_cap}, a.probs,
-                        SMEM ? s_tally : a.tally, a.tables, s_edges, s_widths, AGG};
+    if (lane == 0) s_coop = CoopArgs{TailArgs{a.hist_state, a.hist_draws, a.counts, a.lcg, a.event_cap}, a.probs};
     __syncwarp();
     coop_tail<M, F32>(&s_coop, tab, (uint32_t)(s_pool - s_tally), a.coop_slots, coop_n);
   }
@@ -779,7 +788,7 @@ int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms,
   };
   if (static_smem + dynamic_smem() > (size_t)optin) a.pool_cap = 0;
   if (static_smem + dynamic_smem() > (size_t)optin) a.smem_edges = 0;
-  a.coop_slots = a.pool_cap * (uint32_t)kPoolWords / (uint32_t)kCoopWords;
+  a.coop_slots = coop_slots_of(a.pool_cap * (uint32_t)kPoolWords);
   const size_t smem = dynamic_smem();
   if (static_smem + smem > (size_t)optin) {
     mci::set_error("slab_history_kernel: %u tally slots do not fit in shared memory", a.smem_slots);
