@@ -62,8 +62,8 @@ N_STREAMS_MATERIALISED = 2**22
 # flights; profiles/transport_kernels_instructions_per_flight.md).  Times the
 # measured flights/s, they place a transport workload against the issue peak.
 INST_PER_FLIGHT = {
-    "slab_small_fp64": 777, "slab_small_fp32": 657, "slab_long_fp64": 605, "slab_long_fp32": 477,
-    "batched_fp64": 671, "batched_fp32": 536, "box_fp64": 2292, "box_fp32": 881,
+    "slab_small_fp64": 869, "slab_small_fp32": 739, "slab_long_fp64": 647, "slab_long_fp32": 519,
+    "batched_fp64": 726, "batched_fp32": 599, "box_fp64": 2292, "box_fp32": 881,
     "box_fp64_event": 2697, "box_fp32_event": 1269,
     "pulse_hash": 366, "pulse_stride": 351, "pulse_census": 252,
 }
@@ -258,6 +258,9 @@ def main():
     ap.add_argument("--tally-atomics", type=int, default=0, choices=[0, 1, 2],
                     help="mc_run_config.tally_atomics for --profile-workload (0 library default, 1 per lane, "
                          "2 warp-aggregated)")
+    ap.add_argument("--id-range", default=None,
+                    help="B:E -- run only global histories [B, E) of --profile-workload (mc_run_config.range_*)")
+    ap.add_argument("--block", type=int, default=0, help="mc_run_config.block for --profile-workload (0 default)")
     args = ap.parse_args()
     if args.profile_workload:
         return profile_workload(args)
@@ -441,8 +444,10 @@ def profile_workload(args):
         cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
         tally = mc.Tally(W.tally_slots(probs), len(probs))
         n = sum(p["n_histories"] for p in probs)
+    rb, re_ = (int(v) for v in args.id_range.split(":")) if args.id_range else (0, 0)
     cfg = mc.mc_run_config(precision=1 if "fp32" in name else 0, tally_atomics=args.tally_atomics,
-                           schedule=args.schedule, use_graph=args.schedule)
+                           schedule=args.schedule, use_graph=args.schedule, range_begin=rb, range_end=re_,
+                           block=args.block)
     times = []
     for _ in range(2):
         a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
