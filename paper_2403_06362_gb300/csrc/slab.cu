@@ -243,6 +243,9 @@ constexpr int kCoopHistWords = 16;     // 8-byte words per history record
 constexpr int kCoopWords = 6;          // 8-byte words per event record
 constexpr uint32_t kCoopEvents = 128;  // events per history and round at most
 constexpr uint32_t kCoopMinEvents = 8;
+// shared memory the tail's records get at least (words): room for rounds of
+// kCoopEvents events with one history
+constexpr size_t kCoopAreaWords = (size_t)kCoopMax * kCoopHistWords + (size_t)kCoopWords * (kCoopEvents + 1u);
 
 __device__ __forceinline__ int coop_groups(int nlive) { return nlive <= 1 ? 1 : nlive <= 2 ? 2 : nlive <= 4 ? 4 : 8; }
 
@@ -782,13 +785,18 @@ int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms,
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  auto dynamic_smem = [&a]() {
+  // the pool's memory, which the cooperative tail reuses: at least
+  // kCoopAreaWords when there is a pool
+  auto pool_words = [&a]() {
+    return a.pool_cap ? std::max<size_t>((size_t)a.pool_cap * kPoolWords, kCoopAreaWords) : (size_t)0;
+  };
+  auto dynamic_smem = [&a, &pool_words]() {
     return (SMEM ? (size_t)a.smem_slots * 8u : 0u) + (size_t)a.smem_edges * 16u +  // edges + widths
-           (size_t)a.pool_cap * kPoolWords * 8u;
+           pool_words() * 8u;
   };
   if (static_smem + dynamic_smem() > (size_t)optin) a.pool_cap = 0;
   if (static_smem + dynamic_smem() > (size_t)optin) a.smem_edges = 0;
-  a.coop_slots = coop_slots_of(a.pool_cap * (uint32_t)kPoolWords);
+  a.coop_slots = coop_slots_of((uint32_t)pool_words());
   const size_t smem = dynamic_smem();
   if (static_smem + smem > (size_t)optin) {
     mci::set_error("slab_history_kernel: %u tally slots do not fit in shared memory", a.smem_slots);
