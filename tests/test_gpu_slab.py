@@ -426,3 +426,44 @@ def test_batched_full_size_sampled(env, oracle):
     c = counts_of(tally, len(probs))
     assert np.array_equal(c[:, 0], np.array([p["n_histories"] for p in probs], dtype=np.uint64))
     assert np.array_equal(c[:, 0], c[:, 3] + c[:, 5] + c[:, 6])
+
+
+# The cooperative tail: a launch of a few long-chain histories in blocks of
+# 256 threads ends with every block's last warp holding at most four live
+# histories, which it runs with lane groups (draw-only values ahead, one lane
+# for the chain of positions, the group for the tallies).  Blocks of 32
+# threads have no pool and never take that path, so the two launch shapes
+# must give the same bits; and the oracle fixes both, event caps included
+# (a cap then falls inside a round of the tail).
+def long_few(seeding, n):
+    return W.slab_long(seeding, n_histories=n)
+
+
+@pytest.mark.parametrize("seeding", [W.SEED_HASH, W.SEED_STRIDE])
+@pytest.mark.parametrize("cap", [0, 2500])
+def test_cooperative_tail_matches_oracle(env, oracle, seeding, cap):
+    probs = long_few(seeding, 96)
+    tally, _ = gpu_run(env, probs, block=256, event_cap=cap)
+    size = W.tally_slots(probs)
+    t = np.zeros(size, dtype=np.int64)
+    c = np.zeros(oracle.NCOUNT, dtype=np.uint64)
+    o = oracle.slab_run(olcg(oracle), W.to_oracle_problem(probs[0], oracle), tally=t, counts=c,
+                        per_history=True, event_cap=cap if cap else 2**40)
+    assert np.array_equal(tally.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(tally.hist_draws.cpu().numpy().view(np.uint64), o["hist_draws"])
+    assert np.array_equal(counts_of(tally, 1)[0, :14], c[:14])
+    if cap:
+        assert c[12] > 0  # some histories were capped (MC_C_CAPPED)
+    assert_tally_close(tally.bins.cpu().numpy(), t)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cooperative_tail_same_bits_as_one_lane_path(env, precision):
+    probs = long_few(W.SEED_HASH, 200)
+    coop, _ = gpu_run(env, probs, block=256, precision=precision)
+    plain, _ = gpu_run(env, probs, block=32, precision=precision)
+    import torch
+    assert torch.equal(coop.bins, plain.bins)
+    assert torch.equal(coop.counts, plain.counts)
+    assert torch.equal(coop.hist_state, plain.hist_state)
+    assert torch.equal(coop.hist_draws, plain.hist_draws)
