@@ -376,9 +376,8 @@ __device__ __noinline__ void coop_draws(const CoopArgs* c, const mcd::Affine* ta
 
 // Phase 2, on one lane: the chain of positions through the round's events,
 // until the round ends (kContinue), an event would pass the cap (-1), or the
-// history leaks or is absorbed; each event's inputs are loaded one event
-// ahead, off the chain.  Then the history's record moves on by the events
-// run, and a history that ended is counted and written out.
+// history leaks or is absorbed.  Then the history's record moves on by the
+// events run, and a history that ended is counted and written out.
 template <int M, bool F32>
 __device__ __noinline__ void coop_walk(const CoopArgs* c, const mcd::Affine* tab, uint32_t hist_off,
                                        uint32_t rec_off, uint32_t E) {
@@ -392,20 +391,40 @@ __device__ __noinline__ void coop_walk(const CoopArgs* c, const mcd::Affine* tab
   const uint32_t ok = left < E ? (uint32_t)left : E;
   int out = mcs::kContinue;
   uint32_t e = 0;
+  // Four events at a time while none of them can end the history (no
+  // leak, no absorption, no cap, and in fp32 no guard band): the chain of
+  // additions runs back to back and one branch takes the four.  Otherwise
+  // one event at a time, with the same operations.
   if constexpr (!F32) {
     double x = dval(H.w[CoopHist::kPos]);
     R.x[0] = dbits(x);
-    unsigned long long pn = R.p[0], mn = R.m[0], fn = R.f[0];
-    for (; e < E; ++e) {
-      const unsigned long long pc = pn, mc = mn, fc = fn;
-      if (e + 1u < E) { pn = R.p[e + 1u]; mn = R.m[e + 1u]; fn = R.f[e + 1u]; }
+    for (;;) {
+      if (e + 4u <= ok) {
+        const double p0 = dval(R.p[e]), p1 = dval(R.p[e + 1u]), p2 = dval(R.p[e + 2u]), p3 = dval(R.p[e + 3u]);
+        const long long m0 = (long long)R.m[e], m1 = (long long)R.m[e + 1u], m2 = (long long)R.m[e + 2u],
+                        m3 = (long long)R.m[e + 3u];
+        const unsigned long long a = R.f[e] | R.f[e + 1u] | R.f[e + 2u] | R.f[e + 3u];
+        const double x1 = __dadd_rn(x, p0), x2 = __dadd_rn(x1, p1), x3 = __dadd_rn(x2, p2), x4 = __dadd_rn(x3, p3);
+        if (!(a | mcs::leaves64(p, m0, x1) | mcs::leaves64(p, m1, x2) | mcs::leaves64(p, m2, x3) |
+              mcs::leaves64(p, m3, x4))) {
+          R.x[e + 1u] = dbits(x1);
+          R.x[e + 2u] = dbits(x2);
+          R.x[e + 3u] = dbits(x3);
+          R.x[e + 4u] = dbits(x4);
+          x = x4;
+          e += 4u;
+          continue;
+        }
+      }
+      if (e == E) break;
       if (e == ok) { out = -1; break; }
       double xn;
-      const int f = mcs::advance64(p, x, dval(mc), dval(pc), xn);
+      const int f = mcs::advance64(p, x, dval(R.m[e]), dval(R.p[e]), xn);
       if (f != mcs::kCollide) { out = f; ++e; break; }
       x = xn;
       R.x[e + 1u] = dbits(x);
-      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+      if (R.f[e]) { out = mcs::kAbsorbed; ++e; break; }
+      ++e;
     }
     H.w[CoopHist::kPos] = dbits(x);
     if (out == mcs::kContinue) { H.w[CoopHist::kDir] = R.m[E]; H.w[CoopHist::kW] = R.w[E]; }
@@ -414,19 +433,40 @@ __device__ __noinline__ void coop_walk(const CoopArgs* c, const mcd::Affine* tab
     float xf = lo_of(pos), xlo = hi_of(pos);
     R.x[0] = pos;
     const uint32_t m = c->t.lcg.m;
-    unsigned long long pn = R.p[0], dn = R.d[0], fn = R.f[0];
-    for (; e < E; ++e) {
-      const unsigned long long pc = pn, dc = dn, fc = fn;
-      if (e + 1u < E) { pn = R.p[e + 1u]; dn = R.d[e + 1u]; fn = R.f[e + 1u]; }
+    for (;;) {
+      if (e + 4u <= ok) {
+        const unsigned long long q0 = R.p[e], q1 = R.p[e + 1u], q2 = R.p[e + 2u], q3 = R.p[e + 3u];
+        const float u0 = hi_of(R.d[e]), u1 = hi_of(R.d[e + 1u]), u2 = hi_of(R.d[e + 2u]), u3 = hi_of(R.d[e + 3u]);
+        const unsigned long long a = R.f[e] | R.f[e + 1u] | R.f[e + 2u] | R.f[e + 3u];
+        float h1, l1, h2, l2, h3, l3, h4, l4;
+        mcs::pair_step(xf, xlo, lo_of(q0), hi_of(q0), h1, l1);
+        mcs::pair_step(h1, l1, lo_of(q1), hi_of(q1), h2, l2);
+        mcs::pair_step(h2, l2, lo_of(q2), hi_of(q2), h3, l3);
+        mcs::pair_step(h3, l3, lo_of(q3), hi_of(q3), h4, l4);
+        if (a == 0ull && mcs::plain_collision32(p, u0, h1, l1) && mcs::plain_collision32(p, u1, h2, l2) &&
+            mcs::plain_collision32(p, u2, h3, l3) && mcs::plain_collision32(p, u3, h4, l4)) {
+          R.x[e + 1u] = pack2(h1, l1);
+          R.x[e + 2u] = pack2(h2, l2);
+          R.x[e + 3u] = pack2(h3, l3);
+          R.x[e + 4u] = pack2(h4, l4);
+          xf = h4;
+          xlo = l4;
+          e += 4u;
+          continue;
+        }
+      }
+      if (e == E) break;
       if (e == ok) { out = -1; break; }
+      const unsigned long long pc = R.p[e];
       float xn, xnlo;
-      const int f = mcs::advance32(p, xf, xlo, hi_of(dc), lo_of(pc), hi_of(pc),
+      const int f = mcs::advance32(p, xf, xlo, hi_of(R.d[e]), lo_of(pc), hi_of(pc),
                                    [&] { return mcd::u01<M>(R.m[e], m); }, xn, xnlo);
       if (f != mcs::kCollide) { out = f; ++e; break; }
       xf = xn;
       xlo = xnlo;
       R.x[e + 1u] = pack2(xf, xlo);
-      if (fc) { out = mcs::kAbsorbed; ++e; break; }
+      if (R.f[e]) { out = mcs::kAbsorbed; ++e; break; }
+      ++e;
     }
     H.w[CoopHist::kPos] = pack2(xf, xlo);
     if (out == mcs::kContinue) H.w[CoopHist::kDir] = pack2(hi_of(R.d[E]), lo_of(R.w[E]));

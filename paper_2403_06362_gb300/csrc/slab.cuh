@@ -408,6 +408,12 @@ __device__ __forceinline__ int advance64(const SlabDev& p, double x, double mu, 
   return kCollide;
 }
 
+// advance64's face tests alone: whether xn, the end of a flight with
+// direction bits mb, lies outside the slab.
+__device__ __forceinline__ bool leaves64(const SlabDev& p, long long mb, double xn) {
+  return (mb > 0 && !nn_lt(xn, p.L)) || (mb < 0 && __double_as_longlong(xn) <= 0);
+}
+
 // The tally of that flight: the track from x to xn, to the face it leaves
 // through, or (mu = 0) the whole distance d in the bin holding x.  Every
 // kind of flight ends in the one call of the bin walk, with its ends chosen
@@ -429,12 +435,26 @@ __device__ __forceinline__ void tally64(const SlabDev& p, double x, double xn, d
 // by TwoSum, the low parts' sum rounded once more (a second-order error).
 // Near a face the leak-or-collide decision is made again in fp64 from the
 // flight's uniform, uf() (called only there).
-template <class UF>
-__device__ __forceinline__ int advance32(const SlabDev& p, float xf, float xlo, float muf, float pr, float pe,
-                                         UF uf, float& xn, float& xnlo) {
+__device__ __forceinline__ void pair_step(float xf, float xlo, float pr, float pe, float& xn, float& xnlo) {
   float s0, t0;
   two_sum_f(xf, pr, s0, t0);
   two_sum_f(s0, __fadd_rn(t0, __fadd_rn(xlo, pe)), xn, xnlo);
+}
+
+// The pair's end point is inside the slab and outside the guard bands: the
+// flight collides there (advance32 decides the same, with the same xn, xnlo).
+__device__ __forceinline__ bool plain_collision32(const SlabDev& p, float muf, float xn, float xnlo) {
+  const bool near_hi = muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
+  const bool near_lo = muf < 0.0f && fabsf(xn) <= p.guard_f;
+  const bool leak_hi = muf > 0.0f && (xn > p.L_f || (xn == p.L_f && xnlo >= 0.0f));
+  const bool leak_lo = muf < 0.0f && (xn < 0.0f || (xn == 0.0f && xnlo <= 0.0f));
+  return !(near_hi | near_lo | leak_hi | leak_lo);
+}
+
+template <class UF>
+__device__ __forceinline__ int advance32(const SlabDev& p, float xf, float xlo, float muf, float pr, float pe,
+                                         UF uf, float& xn, float& xnlo) {
+  pair_step(xf, xlo, pr, pe, xn, xnlo);
   // Guard band: re-decide leak vs collide in fp64 near a face.
   const bool near_hi = muf > 0.0f && fabsf(xn - p.L_f) <= p.guard_f;
   const bool near_lo = muf < 0.0f && fabsf(xn) <= p.guard_f;

@@ -467,3 +467,24 @@ def test_cooperative_tail_same_bits_as_one_lane_path(env, precision):
     assert torch.equal(coop.counts, plain.counts)
     assert torch.equal(coop.hist_state, plain.hist_state)
     assert torch.equal(coop.hist_draws, plain.hist_draws)
+
+
+@pytest.mark.parametrize("m", [62, 48])
+@pytest.mark.parametrize("seeding", [W.SEED_HASH, W.SEED_STRIDE])
+def test_other_modulus_with_cooperative_tail(env, oracle, m, seeding):
+    """Another modulus runs the kernels' generic-modulus instantiation, the
+    cooperative tail's included (few long histories, blocks of 256)."""
+    mc, ctx, torch = env
+    probs = long_few(seeding, 64)
+    tally = mc.Tally(W.tally_slots(probs), 1, n_histories=64)
+    cprobs = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+    mc.mc_transport_run(ctx, mc.make_lcg(m=m, g=G, c=CC), cprobs, mc.mc_run_config(block=256), tally.c)
+    torch.cuda.synchronize()
+    t = np.zeros(W.tally_slots(probs), dtype=np.int64)
+    c = np.zeros(oracle.NCOUNT, dtype=np.uint64)
+    o = oracle.slab_run(oracle.Lcg(m=m, pad=0, g=G, c=CC), W.to_oracle_problem(probs[0], oracle), tally=t,
+                        counts=c, per_history=True)
+    assert np.array_equal(tally.hist_state.cpu().numpy().view(np.uint64), o["hist_state"])
+    assert np.array_equal(tally.hist_draws.cpu().numpy().view(np.uint64), o["hist_draws"])
+    assert np.array_equal(counts_of(tally, 1)[0, :14], c[:14])
+    assert_tally_close(tally.bins.cpu().numpy(), t)
