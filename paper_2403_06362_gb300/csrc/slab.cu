@@ -234,10 +234,11 @@ __device__ __forceinline__ void end_history(const TailArgs& t, const mcs::Rng<M>
 //   3. the group's lanes make the tally contributions of the round's events.
 // Every value comes from the same function, with the same operands, as in
 // the one-lane path, so the draws, tallies and counters are the same bits.
-// The histories' state, the launch's arguments and the rounds' event
-// records sit in the (then empty) pool's shared memory, and each phase is a
-// function of its own that takes them from there: the main loop has ended,
-// and almost nothing stays in registers across the calls.
+// The histories' state and the rounds' event records sit in the (then
+// empty) pool's shared memory, the launch's arguments in a small shared
+// record, and each phase is a function of its own that takes them from
+// there: the main loop has ended, and almost nothing stays in registers
+// across the calls.
 constexpr int kCoopMax = 4;            // live histories at most
 constexpr int kCoopHistWords = 16;     // 8-byte words per history record
 constexpr int kCoopWords = 6;          // 8-byte words per event record
