@@ -181,7 +181,7 @@ __device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, doub
     // the last [e_j, b]; only the ends take an fp64 difference.
     double e1 = s.edges[j + 1];
     const double hi = nn_lt(b, e1) ? b : e1;
-    if (nn_lt(a, hi)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(hi, a), w_fix)));
+    if (nn_lt(a, hi)) s.add(j, mcx::llrint_nonneg(__dmul_rn(__dsub_rn(hi, a), w_fix)));
     if (!nn_lt(e1, b) || j + 1 >= nb) return;
     for (++j;; ++j) {
       e1 = s.edges[j + 1];
@@ -190,14 +190,14 @@ __device__ __forceinline__ void seg64(const SlabDev& p, double a, double b, doub
       if (!nn_lt(e1, b) || j + 1 >= nb) return;
     }
     const double ej = s.edges[j];
-    if (nn_lt(ej, b)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(b, ej), w_fix)));
+    if (nn_lt(ej, b)) s.add(j, mcx::llrint_nonneg(__dmul_rn(__dsub_rn(b, ej), w_fix)));
     return;
   }
   double lo = a;
   for (;;) {
     const double e1 = edge_of(p, s, j + 1);
     const double hi = nn_lt(b, e1) ? b : e1;
-    if (nn_lt(lo, hi)) s.add(j, __double2ll_rn(__dmul_rn(__dsub_rn(hi, lo), w_fix)));
+    if (nn_lt(lo, hi)) s.add(j, mcx::llrint_nonneg(__dmul_rn(__dsub_rn(hi, lo), w_fix)));
     if (!nn_lt(e1, b) || j + 1 >= nb) break;
     lo = e1;
     ++j;
