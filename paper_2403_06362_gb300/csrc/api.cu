@@ -556,6 +556,14 @@ int run_slab_graph(mc_ctx* ctx, const mc_lcg* lcg, const mc_problem* problems, u
   key = fnv(key, &n_problems, sizeof n_problems);
   key = fnv(key, &bytes, sizeof bytes);
   key = fnv(key, &tally->n_slots, sizeof tally->n_slots);
+  // the history range and the launch's shape are baked into the graph (the
+  // kernel's ticket bound, its grid, chunk and block): a call whose problems
+  // hold another number of histories captures a graph of its own
+  key = fnv(key, &L.range_begin, sizeof L.range_begin);
+  key = fnv(key, &L.total, sizeof L.total);
+  key = fnv(key, &L.chunk, sizeof L.chunk);
+  key = fnv(key, &L.block, sizeof L.block);
+  key = fnv(key, &L.single_n_bins, sizeof L.single_n_bins);
   if (!ctx->graphs) ctx->graphs = new mci::GraphCache();
   auto it = ctx->graphs->m.find(key);
   cudaGraphExec_t exec = nullptr;

@@ -399,6 +399,24 @@ def test_history_graph_replay_with_new_problem_data(env):
         _same_bits(ref, tally, len(probs))
 
 
+def test_history_graph_with_other_history_counts(env):
+    """The same problem shapes with other history counts: the history range
+    is baked into a captured launch, so each count gets its own graph."""
+    mc, ctx, torch = env
+    tally = None  # one tally for every call: the same buffers, so only the counts differ
+    for n in (3000, 7000, 3000, 12000):
+        probs = W.slab_batched(W.SEED_HASH_HIER, n_problems=8, max_histories=n, seed=5)
+        for p in probs:
+            p["n_histories"] = n
+        if tally is None:
+            tally = mc.Tally(W.tally_slots(probs), len(probs))
+        cp = mc.problem_array([W.to_mc_problem(p, mc) for p in probs])
+        mc.mc_transport_run(ctx, mc.make_lcg(), cp, mc.mc_run_config(use_graph=1), tally.c)
+        torch.cuda.synchronize()
+        ref, _ = gpu_run(env, probs, n_hist_out=False)
+        _same_bits(ref, tally, len(probs))
+
+
 def test_tally_overflow_reported(env):
     mc, ctx, torch = env
     probs = W.slab_small(W.SEED_HASH, n_histories=100)
