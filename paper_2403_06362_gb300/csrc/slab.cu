@@ -575,7 +575,7 @@ __device__ __noinline__ void coop_tail(const CoopArgs* c, const mcd::Affine* tab
 }
 
 template <int M, bool F32, bool SMEM, bool AGG>
-__global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
+__device__ __forceinline__ void slab_history_body(const RunArgs& a) {
   extern __shared__ unsigned long long s_tally[];
   __shared__ mcd::Affine tab[64];
   if (threadIdx.x == 0) {
@@ -809,9 +809,29 @@ __global__ void __launch_bounds__(512, 2) slab_history_kernel(const RunArgs a) {
   }
 }
 
+// The kernel in two register budgets.  The fp32 flight fits 64 registers
+// (four blocks of 256 per SM); the fp64 flight spills there, and runs faster
+// with 80 and three blocks per SM (slab_long 240 -> 215 ms, batched 23.4 ->
+// 20.6 ms; the fp32 kernel at 80 measured batched 18.0 -> 19.8 ms).  Both
+// accept blocks of up to 512 threads.
+template <int M, bool F32, bool SMEM, bool AGG>
+__global__ void __launch_bounds__(512, 2) slab_history_kernel_f32(const RunArgs a) {
+  slab_history_body<M, F32, SMEM, AGG>(a);
+}
+template <int M, bool F32, bool SMEM, bool AGG>
+__global__ void __maxnreg__(80) slab_history_kernel_f64(const RunArgs a) {
+  slab_history_body<M, F32, SMEM, AGG>(a);
+}
+
+template <int M, bool F32, bool SMEM, bool AGG>
+auto history_kernel_of() {
+  if constexpr (F32) return slab_history_kernel_f32<M, F32, SMEM, AGG>;
+  else return slab_history_kernel_f64<M, F32, SMEM, AGG>;
+}
+
 template <int M, bool F32, bool SMEM, bool AGG>
 int launch_history(const RunArgs& a0, int block, int blocks_per_sm, int num_sms, cudaStream_t s) {
-  auto k = slab_history_kernel<M, F32, SMEM, AGG>;
+  auto k = history_kernel_of<M, F32, SMEM, AGG>();
   RunArgs a = a0;
   // Static shared memory of this instantiation (read once) and the device's
   // opt-in limit: what does not fit beside them is given up, the compaction
