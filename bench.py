@@ -62,8 +62,8 @@ N_STREAMS_MATERIALISED = 2**22
 # flights; profiles/transport_kernels_instructions_per_flight.md).  Times the
 # measured flights/s, they place a transport workload against the issue peak.
 INST_PER_FLIGHT = {
-    "slab_small_fp64": 917, "slab_small_fp32": 741, "slab_long_fp64": 690, "slab_long_fp32": 523,
-    "batched_fp64": 778, "batched_fp32": 604, "box_fp64": 2292, "box_fp32": 881,
+    "slab_small_fp64": 883, "slab_small_fp32": 741, "slab_long_fp64": 689, "slab_long_fp32": 523,
+    "batched_fp64": 764, "batched_fp32": 604, "box_fp64": 2292, "box_fp32": 881,
     "box_fp64_event": 2697, "box_fp32_event": 1269,
     "pulse_hash": 366, "pulse_stride": 351, "pulse_census": 252,
 }
