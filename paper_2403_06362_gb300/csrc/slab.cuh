@@ -430,11 +430,9 @@ __device__ __forceinline__ void tally64(const SlabDev& p, double x, double xn, d
   seg64(p, a, b, w_mu, s);
 }
 
-// The end of a flight of the fp32 path: xn + xnlo = (xf + xlo) + d muf, with
-// pr = d muf rounded and pe its exact error (a fused multiply-add); the sum
-// by TwoSum, the low parts' sum rounded once more (a second-order error).
-// Near a face the leak-or-collide decision is made again in fp64 from the
-// flight's uniform, uf() (called only there).
+// The fp32 path's position step: xn + xnlo = (xf + xlo) + d muf, with pr =
+// d muf rounded and pe its exact error (a fused multiply-add); the sum by
+// TwoSum, the low parts' sum rounded once more (a second-order error).
 __device__ __forceinline__ void pair_step(float xf, float xlo, float pr, float pe, float& xn, float& xnlo) {
   float s0, t0;
   two_sum_f(xf, pr, s0, t0);
@@ -451,6 +449,9 @@ __device__ __forceinline__ bool plain_collision32(const SlabDev& p, float muf, f
   return !(near_hi | near_lo | leak_hi | leak_lo);
 }
 
+// The end of a flight of the fp32 path by pair_step, and whether it leaves
+// the slab; near a face the leak-or-collide decision is made again in fp64
+// from the flight's uniform, uf() (called only there).
 template <class UF>
 __device__ __forceinline__ int advance32(const SlabDev& p, float xf, float xlo, float muf, float pr, float pe,
                                          UF uf, float& xn, float& xnlo) {
@@ -478,6 +479,7 @@ __device__ __forceinline__ int advance32(const SlabDev& p, float xf, float xlo, 
   return leak_hi ? kLeakHi : (leak_lo ? kLeakLo : kCollide);
 }
 
+// tally64's counterpart for the fp32 path, on position pairs.
 __device__ __forceinline__ void tally32(const SlabDev& p, float xf, float xlo, float xn, float xnlo, float muf,
                                         float d, float wf, int outcome, const Sink& s) {
   if (outcome == kCollide && muf == 0.0f) { point32(p, xf, d, s); return; }
